@@ -1,0 +1,128 @@
+/*
+ * jdec.h -- C ABI of the GB300 (sm_103a) back-end of baseline JPEG decoding.
+ *
+ * The library runs the data-parallel part of the decoder path of Fig. 1
+ * (Sodsong et al., PMAM'14, Sec. 2): per-component dequantisation, the 8x8
+ * fixed-point IDCT as a column pass (Eq. 1) followed by a row pass (Eq. 2)
+ * with range-limit clamping (Sec. 4.1), chroma upsampling by replication or
+ * by the triangular filter of Alg. 1 (Sec. 4.2; 4:2:2 as printed, 4:2:0 as the
+ * separable extension), and YCbCr -> RGB by Alg. 2 in 16-bit fixed point
+ * (Sec. 4.3), writing interleaved RGB in raster order (Sec. 4.3, Fig. 3-4).
+ * Entropy (Huffman) decoding stays on the host (Sec. 2, Sec. 4.5) and is not
+ * part of this interface: callers pass entropy-decoded coefficients.
+ *
+ * Input layout (Sec. 4: "Y blocks followed by Cb blocks followed by Cr
+ * blocks"; "an array of short"): one int16 plane per component, blocks in
+ * block-row-major order over the padded MCU grid, 64 coefficients per block in
+ * natural order (index 8*v + u: row v = vertical frequency, column u =
+ * horizontal frequency; zig-zag already undone).  For an image of W x H with
+ * Hmax = max h_samp, Vmax = max v_samp: MCUs_x = ceil(W / (8*Hmax)),
+ * MCUs_y = ceil(H / (8*Vmax)), component c has blocks_w[c] = MCUs_x*h_samp[c]
+ * by blocks_h[c] = MCUs_y*v_samp[c] blocks.  The MCU is 8x8 pixels for 4:4:4
+ * and 16x8 for 4:2:2 (Sec. 2), 16x16 for 4:2:0.
+ *
+ * Output: 8-bit interleaved R,G,B, rgb_pitch bytes between rows; only the
+ * W x H pixels are written, padding bytes of a row are left untouched.
+ *
+ * The integer result is fully specified (two's-complement int32 wrap,
+ * arithmetic shifts, fixed multipliers) and is bit-identical to the CPU
+ * oracle for every input; see the repository's design notes for the exact
+ * arithmetic.
+ *
+ * Threading: a context is not thread-safe; use one per host thread.  All
+ * decode calls are asynchronous on the given stream (a cudaStream_t passed as
+ * void*; NULL = the legacy default stream).  Argument errors are reported
+ * synchronously and launch nothing.
+ */
+#ifndef JDEC_H
+#define JDEC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define JDEC_API __attribute__((visibility("default")))
+#else
+#define JDEC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct jdec_ctx jdec_ctx;
+
+typedef enum {
+    JDEC_OK = 0,
+    JDEC_EINVAL = -1,        /* invalid argument or inconsistent geometry   */
+    JDEC_ENOMEM = -2,        /* device or pinned-host allocation failed     */
+    JDEC_ECUDA = -3,         /* a CUDA runtime call failed                  */
+    JDEC_EUNSUPPORTED = -4,  /* valid JPEG, but a sampling this build lacks */
+    JDEC_EBUSY = -5,         /* request exceeds the context's HBM budget    */
+    JDEC_ETIMEOUT = -6       /* a device-side bounded wait gave up          */
+} jdec_status;
+
+/* Upsampling selection (jdec_image.flags).  Fancy = triangular filter
+ * (Alg. 1; default), replicate = nearest chroma sample. */
+#define JDEC_UPSAMPLE_FANCY     0u
+#define JDEC_UPSAMPLE_REPLICATE 1u
+
+typedef struct {
+    int device;               /* CUDA device ordinal                         */
+    size_t hbm_budget_bytes;  /* 0 = no limit; bounds context-owned buffers  */
+    int max_batch;            /* 0 = default (4096); images per batch call   */
+    int autotune;             /* 1 = time tile shapes on first use per shape */
+    const char *tune_file;    /* NULL or a JSON file to load/save tile picks */
+} jdec_options;               /* a NULL options pointer = all defaults       */
+
+typedef struct {
+    int32_t width, height;        /* pixels, 1..65535                          */
+    int32_t ncomp;                /* must be 3 (Y, Cb, Cr)                     */
+    uint8_t h_samp[3], v_samp[3]; /* luma (1,1) | (2,1) | (2,2); chroma (1,1)  */
+    const int16_t *coef[3];       /* DEVICE pointers, 16-byte aligned, planes
+                                     as described above                         */
+    int32_t blocks_w[3], blocks_h[3]; /* must equal MCUs_x*h, MCUs_y*v         */
+    const uint16_t *qtab[3];      /* HOST pointers, 64 entries, natural order;
+                                     read during the call, not retained         */
+    uint8_t *rgb;                 /* DEVICE pointer to the RGB output          */
+    int64_t rgb_pitch;            /* bytes per output row, >= 3*width          */
+    uint32_t flags;               /* JDEC_UPSAMPLE_*                           */
+} jdec_image;
+
+/* Creates a context on opt->device (default 0).  *out receives the context. */
+JDEC_API jdec_status jdec_create(jdec_ctx **out, const jdec_options *opt);
+
+/* Decodes one image with one launch of the fused kernel on `stream`.
+ * Coefficient and RGB buffers are owned by the caller and must stay valid
+ * until the stream has executed the launch.  Returns JDEC_EINVAL without
+ * launching for inconsistent descriptions (see jdec_image). */
+JDEC_API jdec_status jdec_decode_coeffs(jdec_ctx *ctx, const jdec_image *img, void *stream);
+
+/* Decodes n images (any mix of sizes and samplings) with one persistent launch
+ * over a flattened MCU work list.  The launch is recorded once per work-list
+ * shape as a CUDA graph and replayed with the descriptors of each call.
+ * Per-image results are identical to jdec_decode_coeffs.  n <= max_batch. */
+JDEC_API jdec_status jdec_decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int32_t n, void *stream);
+
+/* Same as jdec_decode_coeffs, but coef[] and rgb point to HOST memory
+ * (page-locked for full speed).  The library copies the planes to device
+ * buffers it owns, decodes, and copies the RGB back, all on `stream`, in
+ * row bands so that copies overlap decoding.  The host buffers must stay
+ * valid until the stream has executed the copies. */
+JDEC_API jdec_status jdec_decode_host(jdec_ctx *ctx, const jdec_image *img, void *stream);
+
+/* Synchronises `stream` and reports any device-side error recorded by earlier
+ * launches of this context (a bounded wait that gave up -> JDEC_ETIMEOUT).
+ * Clears the recorded error. */
+JDEC_API jdec_status jdec_sync_status(jdec_ctx *ctx, void *stream);
+
+/* Releases the context and every buffer, graph and tensor map it owns. */
+JDEC_API jdec_status jdec_destroy(jdec_ctx *ctx);
+
+/* Static description of a status code. */
+JDEC_API const char *jdec_status_str(jdec_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JDEC_H */

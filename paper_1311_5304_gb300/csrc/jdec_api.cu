@@ -1,0 +1,330 @@
+// jdec_api.cu -- host runtime behind the C ABI declared in include/jdec.h:
+// validation, tile choice, TMA tensor-map encoding, launches, host-buffer
+// staging and the device error word.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/jdec.h"
+#include "jdec_common.h"
+#include "jdec_launch.h"
+#include "jdec_runtime.h"
+
+using namespace jdec;
+
+namespace jdec {
+
+const char *status_str(jdec_status s)
+{
+    switch (s) {
+    case JDEC_OK: return "ok";
+    case JDEC_EINVAL: return "invalid argument";
+    case JDEC_ENOMEM: return "out of memory";
+    case JDEC_ECUDA: return "CUDA error";
+    case JDEC_EUNSUPPORTED: return "unsupported sampling";
+    case JDEC_EBUSY: return "exceeds the HBM budget";
+    case JDEC_ETIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+// Makes `device` current for the lifetime of the guard, restoring the
+// caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int device)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != device && cudaSetDevice(device) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 3-D view {64 coefficients, blocks_w, blocks_h} of one plane, box
+// {64, box_w, box_h}, 128-byte swizzle (conflict-free thread-per-block reads).
+// The element type is declared as uint16: TMA only moves the bytes.
+bool encode_plane_map(CUtensorMap *m, const int16_t *base, int bw, int bh, int box_w, int box_h)
+{
+    auto enc = get_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {64, static_cast<cuuint64_t>(bw), static_cast<cuuint64_t>(bh)};
+    cuuint64_t strides[2] = {128, static_cast<cuuint64_t>(bw) * 128};
+    cuuint32_t box[3] = {64, static_cast<cuuint32_t>(box_w), static_cast<cuuint32_t>(box_h)};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<int16_t *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers)
+{
+    if (!img) return JDEC_EINVAL;
+    if (img->width < 1 || img->width > 65535 || img->height < 1 || img->height > 65535) return JDEC_EINVAL;
+    if (img->ncomp != 3) return img->ncomp == 1 ? JDEC_EUNSUPPORTED : JDEC_EINVAL;
+    for (int c = 0; c < 3; ++c)
+        if (img->h_samp[c] < 1 || img->h_samp[c] > 4 || img->v_samp[c] < 1 || img->v_samp[c] > 4) return JDEC_EINVAL;
+    if (img->h_samp[1] != 1 || img->v_samp[1] != 1 || img->h_samp[2] != 1 || img->v_samp[2] != 1)
+        return JDEC_EUNSUPPORTED;
+    const int hm = img->h_samp[0], vm = img->v_samp[0];
+    if (!((hm == 1 && vm == 1) || (hm == 2 && vm == 1) || (hm == 2 && vm == 2))) return JDEC_EUNSUPPORTED;
+    if (img->flags & ~JDEC_UPSAMPLE_REPLICATE) return JDEC_EINVAL;
+    g->hm = hm; g->vm = vm;
+    g->fancy = (img->flags & JDEC_UPSAMPLE_REPLICATE) == 0 && hm == 2;
+    g->W = img->width; g->H = img->height;
+    g->mcus_x = (img->width + 8 * hm - 1) / (8 * hm);
+    g->mcus_y = (img->height + 8 * vm - 1) / (8 * vm);
+    g->cw = (img->width + hm - 1) / hm;
+    g->ch = (img->height + vm - 1) / vm;
+    for (int c = 0; c < 3; ++c) {
+        const int h = c ? 1 : hm, v = c ? 1 : vm;
+        if (img->blocks_w[c] != g->mcus_x * h || img->blocks_h[c] != g->mcus_y * v) return JDEC_EINVAL;
+        if (!img->coef[c] || !img->qtab[c]) return JDEC_EINVAL;
+        if (!host_buffers && (reinterpret_cast<uintptr_t>(img->coef[c]) & 15)) return JDEC_EINVAL;
+    }
+    if (!img->rgb || img->rgb_pitch < 3 * static_cast<int64_t>(img->width)) return JDEC_EINVAL;
+    g->coef_bytes = 0;
+    for (int c = 0; c < 3; ++c) g->coef_bytes += static_cast<int64_t>(img->blocks_w[c]) * img->blocks_h[c] * 128;
+    g->rgb_bytes = 3 * static_cast<int64_t>(img->width) * img->height;
+    return JDEC_OK;
+}
+
+// Strip width (MCUs) and chunk height (MCU rows) for `nrows` MCU rows of an
+// image: enough work items to fill every SM at the kernel's occupancy.
+void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int *wt, int *rpc, int *nchunks,
+                int *smem)
+{
+    int w = force_wt > 0 ? force_wt : tuned_wt(ctx, g);
+    if (w <= 0) w = (g.hm == 1) ? 16 : (g.vm == 1 ? 12 : 8);
+    w = std::max(1, std::min(w, kMaxWT));
+    const SmemLayout L = smem_layout(g.hm, g.vm, g.fancy, w);
+    const int occ = occupancy_cached(ctx, g.hm, g.vm, g.fancy, L.total);
+    const int nstrips = (g.mcus_x + w - 1) / w;
+    const long target = static_cast<long>(occ) * ctx->sms;
+    int nch = static_cast<int>(std::max<long>(1, (target + nstrips - 1) / nstrips));
+    nch = std::min(nch, nrows);
+    int r = (nrows + nch - 1) / nch;
+    const int min_rows = (g.fancy && g.vm == 2) ? 4 : 1;   // amortise the chroma prologue
+    r = std::max(r, std::min(min_rows, nrows));
+    *wt = w;
+    *rpc = r;
+    *nchunks = (nrows + r - 1) / r;
+    *smem = L.total;
+}
+
+void fill_desc(ImageDesc *d, const jdec_image *img, const Geometry &g, int wt, int rpc, int nchunks)
+{
+    memset(d, 0, sizeof(*d));
+    d->rgb = img->rgb;
+    d->pitch = img->rgb_pitch;
+    d->W = g.W; d->H = g.H;
+    d->mcus_x = g.mcus_x; d->mcus_y = g.mcus_y;
+    d->cw = g.cw; d->ch = g.ch;
+    d->wt = wt;
+    d->nstrips = (g.mcus_x + wt - 1) / wt;
+    d->rows_per_chunk = rpc;
+    d->nchunks = nchunks;
+    d->row0 = 0;
+    d->row1 = g.mcus_y;
+    d->aligned8 = ((reinterpret_cast<uintptr_t>(img->rgb) | static_cast<uintptr_t>(img->rgb_pitch)) & 7) == 0;
+    for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < 64; ++k) d->q[c][k] = img->qtab[c][k];
+}
+
+bool encode_maps(CUtensorMap maps[3], const jdec_image *img, const Geometry &g, int wt)
+{
+    const int halo = g.fancy ? 1 : 0;
+    if (!encode_plane_map(&maps[0], img->coef[0], img->blocks_w[0], img->blocks_h[0], g.hm * wt, g.vm)) return false;
+    for (int c = 1; c < 3; ++c)
+        if (!encode_plane_map(&maps[c], img->coef[c], img->blocks_w[c], img->blocks_h[c], wt + 2 * halo, 1))
+            return false;
+    return true;
+}
+
+jdec_status launch_rows(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cudaStream_t s, int row0,
+                        int row1, int force_wt)
+{
+    if (row1 <= row0) return JDEC_OK;
+    int wt, rpc, nchunks, smem;
+    plan_tiles(ctx, g, row1 - row0, force_wt, &wt, &rpc, &nchunks, &smem);
+    DecodeParams p;
+    memset(&p, 0, sizeof(p));
+    if (!encode_maps(p.tmap, img, g, wt)) return JDEC_ECUDA;
+    fill_desc(&p.img, img, g, wt, rpc, nchunks);
+    p.img.row0 = row0;
+    p.img.row1 = row1;
+    p.err = ctx->d_err;
+    const int grid = p.img.nstrips * nchunks;
+    cudaError_t e = launch_fused(g.hm, g.vm, g.fancy, p, grid, smem, s);
+    if (e != cudaSuccess) return JDEC_ECUDA;
+    ctx->launches++;
+    return JDEC_OK;
+}
+
+jdec_status launch_image(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cudaStream_t s, int force_wt)
+{
+    return launch_rows(ctx, img, g, s, 0, g.mcus_y, force_wt);
+}
+
+int occupancy_cached(jdec_ctx *ctx, int hm, int vm, bool fancy, int smem)
+{
+    const int v = (hm == 1) ? 0 : (vm == 1 ? (fancy ? 2 : 1) : (fancy ? 4 : 3));
+    for (int i = 0; i < ctx->n_occ; ++i)
+        if (ctx->occ_key[i][0] == v && ctx->occ_key[i][1] == smem) return ctx->occ_val[i];
+    const int o = fused_occupancy(hm, vm, fancy, smem);
+    if (ctx->n_occ < static_cast<int>(sizeof(ctx->occ_val) / sizeof(ctx->occ_val[0]))) {
+        ctx->occ_key[ctx->n_occ][0] = v;
+        ctx->occ_key[ctx->n_occ][1] = smem;
+        ctx->occ_val[ctx->n_occ] = o;
+        ctx->n_occ++;
+    }
+    return o;
+}
+
+jdec_status ensure_buffer(jdec_ctx *ctx, void **buf, size_t *cap, size_t need)
+{
+    if (*cap >= need) return JDEC_OK;
+    const size_t others = ctx->owned_bytes - *cap;
+    if (ctx->opt.hbm_budget_bytes && others + need > ctx->opt.hbm_budget_bytes) return JDEC_EBUSY;
+    if (*buf) cudaFree(*buf);
+    ctx->owned_bytes -= *cap;
+    *buf = nullptr;
+    *cap = 0;
+    if (cudaMalloc(buf, need) != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        return JDEC_ENOMEM;
+    }
+    *cap = need;
+    ctx->owned_bytes += need;
+    return JDEC_OK;
+}
+
+}  // namespace jdec
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *jdec_status_str(jdec_status s) { return jdec::status_str(s); }
+
+jdec_status jdec_create(jdec_ctx **out, const jdec_options *opt)
+{
+    if (!out) return JDEC_EINVAL;
+    *out = nullptr;
+    jdec_options o;
+    memset(&o, 0, sizeof(o));
+    if (opt) o = *opt;
+    if (o.max_batch <= 0) o.max_batch = 4096;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) {
+        cudaGetLastError();
+        return ndev == 0 ? JDEC_ECUDA : JDEC_EINVAL;
+    }
+    DeviceGuard dg(o.device);
+    if (!dg.ok) return JDEC_ECUDA;
+    if (!jdec::get_encoder()) return JDEC_ECUDA;
+    jdec_ctx *ctx = new (std::nothrow) jdec_ctx();
+    if (!ctx) return JDEC_ENOMEM;
+    ctx->opt = o;
+    ctx->device = o.device;
+    if (cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, o.device) != cudaSuccess) {
+        delete ctx;
+        return JDEC_ECUDA;
+    }
+    if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->d_err) cudaFree(ctx->d_err);
+        delete ctx;
+        return JDEC_ENOMEM;
+    }
+    jdec::load_tune_table(ctx);
+    *out = ctx;
+    return JDEC_OK;
+}
+
+jdec_status jdec_decode_coeffs(jdec_ctx *ctx, const jdec_image *img, void *stream)
+{
+    if (!ctx) return JDEC_EINVAL;
+    jdec::Geometry g;
+    jdec_status st = jdec::validate(img, &g, false);
+    if (st != JDEC_OK) return st;
+    jdec::DeviceGuard dg(ctx->device);
+    if (!dg.ok) return JDEC_ECUDA;
+    if (ctx->opt.autotune) jdec::autotune_shape(ctx, img, g, static_cast<cudaStream_t>(stream));
+    return jdec::launch_image(ctx, img, g, static_cast<cudaStream_t>(stream), 0);
+}
+
+jdec_status jdec_decode_host(jdec_ctx *ctx, const jdec_image *img, void *stream)
+{
+    if (!ctx) return JDEC_EINVAL;
+    jdec::Geometry g;
+    jdec_status st = jdec::validate(img, &g, true);
+    if (st != JDEC_OK) return st;
+    jdec::DeviceGuard dg(ctx->device);
+    if (!dg.ok) return JDEC_ECUDA;
+    return jdec::decode_host_banded(ctx, img, g, static_cast<cudaStream_t>(stream));
+}
+
+jdec_status jdec_decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int32_t n, void *stream)
+{
+    if (!ctx || n < 0 || (n > 0 && !imgs) || n > ctx->opt.max_batch) return JDEC_EINVAL;
+    if (n == 0) return JDEC_OK;
+    jdec::DeviceGuard dg(ctx->device);
+    if (!dg.ok) return JDEC_ECUDA;
+    return jdec::decode_batch(ctx, imgs, n, static_cast<cudaStream_t>(stream));
+}
+
+jdec_status jdec_sync_status(jdec_ctx *ctx, void *stream)
+{
+    if (!ctx) return JDEC_EINVAL;
+    jdec::DeviceGuard dg(ctx->device);
+    if (!dg.ok) return JDEC_ECUDA;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return JDEC_ECUDA;
+    int h = 0;
+    if (cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return JDEC_ECUDA;
+    if (h != 0) {
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        return JDEC_ETIMEOUT;
+    }
+    return JDEC_OK;
+}
+
+jdec_status jdec_destroy(jdec_ctx *ctx)
+{
+    if (!ctx) return JDEC_EINVAL;
+    {
+        jdec::DeviceGuard dg(ctx->device);
+        jdec::release_runtime(ctx);
+        if (ctx->d_err) cudaFree(ctx->d_err);
+    }
+    delete ctx;
+    return JDEC_OK;
+}
+
+}  // extern "C"

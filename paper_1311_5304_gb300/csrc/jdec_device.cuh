@@ -1,0 +1,282 @@
+// jdec_device.cuh -- device building blocks of the fused back-end kernel:
+// PTX wrappers (TMA, mbarrier, saturating pack), the 1-D integer IDCT, the
+// per-block 2-D IDCT over a TMA-swizzled tile, and the per-8-pixel
+// upsampling + colour-conversion stage.
+//
+// Integer arithmetic (Sec. 4.1, Eq. 1 column pass then Eq. 2 row pass):
+// the 1-D transform y = M x uses the 13-bit fixed-point matrix of the
+// Loeffler-Ligtenberg-Moschytz flowgraph (multipliers round(k * 2^13) of the
+// twelve cosine expressions), written here in its collapsed even/odd form:
+//   even:  e0 = 8192(x0 + x4) + 10703 x2 +  4433 x6     e3 = ... - (b0)
+//          e1 = 8192(x0 - x4) +  4433 x2 - 10704 x6     e2 = ... - (b1)
+//   odd:   o_n = sum_k O[n][k] x_k over k = 1, 3, 5, 7
+//   y_n = e_n + o_n,  y_{7-n} = e_n - o_n
+// Every entry is an exact integer combination of the flowgraph's products,
+// so the sums are identical mod 2^32 to evaluating the flowgraph itself.
+// Column pass: (y + 2^10) >> 11.  Row pass: (y + 2^17 + 128 * 2^18) >> 18,
+// saturated to [0, 255].  int32 arithmetic wraps (two's complement).
+#pragma once
+
+#include <cstdint>
+#include <cuda.h>
+#include "jdec_common.h"
+
+namespace jdec {
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on an mbarrier phase: returns false if `budget_ns` passed
+// without the phase completing (the caller then reports kErrTimeout).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t budget_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63) == 0 && global_timer_ns() - t0 > budget_ns) return false;
+        if (it > (1u << 30)) return false;
+    }
+}
+
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 3-D tiled TMA load into shared memory, completion counted on `bar`.
+// Coordinates are element indices {inner, block column, block row}; the
+// inner coordinate is always 0 (16-byte aligned by construction).
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int c0, int c1, int c2)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cta.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch_map(const CUtensorMap *map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+__device__ __forceinline__ uint4 lds128(uint32_t a)
+{
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(a));
+    return v;
+}
+
+// Saturate four int32 to [0, 255] and pack them as bytes [a, b, c, d].
+__device__ __forceinline__ uint32_t pack_sat4(int a, int b, int c, int d)
+{
+    uint32_t t, r;
+    asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(t) : "r"(d), "r"(c), "r"(0u));
+    asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(b), "r"(a), "r"(t));
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// 1-D transform (see the header comment).  `rnd` is added to the even
+// butterfly inputs, so every output carries it exactly once.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void idct8(const int x0, const int x1, const int x2, const int x3,
+                                      const int x4, const int x5, const int x6, const int x7,
+                                      const int rnd, int y[8])
+{
+    const int a0 = (x0 + x4) * 8192 + rnd;
+    const int a1 = (x0 - x4) * 8192 + rnd;
+    const int b0 = x2 * 10703 + x6 * 4433;
+    const int b1 = x2 * 4433 - x6 * 10704;
+    const int e0 = a0 + b0, e3 = a0 - b0;
+    const int e1 = a1 + b1, e2 = a1 - b1;
+    const int o0 = x1 * 11363 + x3 * 9633 + x5 * 6437 + x7 * 2260;
+    const int o1 = x1 * 9633 - x3 * 2259 - x5 * 11362 - x7 * 6436;
+    const int o2 = x1 * 6437 - x3 * 11362 + x5 * 2261 + x7 * 9633;
+    const int o3 = x1 * 2260 - x3 * 6436 + x5 * 9633 - x7 * 11363;
+    y[0] = e0 + o0; y[7] = e0 - o0;
+    y[1] = e1 + o1; y[6] = e1 - o1;
+    y[2] = e2 + o2; y[5] = e2 - o2;
+    y[3] = e3 + o3; y[4] = e3 - o3;
+}
+
+__device__ __forceinline__ int sext_lo(uint32_t w) { return static_cast<int>(static_cast<int16_t>(w & 0xffffu)); }
+__device__ __forceinline__ int sext_hi(uint32_t w) { return static_cast<int>(w) >> 16; }
+
+// Dequantise + 2-D IDCT one block that TMA placed at shared address `blk`
+// with the 128-byte swizzle (16-byte chunk c of the 128-byte row at address
+// A lives at chunk c ^ ((A >> 7) & 7)).  q: dequantisation table (int32,
+// natural order, shared memory).  Writes the 8x8 samples to `dst` (shared
+// memory, row pitch `pitch` bytes, 8-byte aligned rows).
+__device__ __forceinline__ void idct_block(uint32_t blk, const int *__restrict__ q, uint8_t *dst, int pitch)
+{
+    const uint32_t sw = (blk >> 7) & 7u;
+    uint32_t w[8][4];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const uint4 r = lds128(blk + ((static_cast<uint32_t>(v) ^ sw) << 4));
+        w[v][0] = r.x; w[v][1] = r.y; w[v][2] = r.z; w[v][3] = r.w;
+    }
+    // Eq. 1: column pass over the vertical frequency v for each u.
+    int ws[8][8];   // [y][u], 2 fractional bits
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        int x[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const uint32_t word = w[v][u >> 1];
+            x[v] = ((u & 1) ? sext_hi(word) : sext_lo(word)) * q[v * 8 + u];
+        }
+        int y[8];
+        idct8(x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7], 1 << 10, y);
+#pragma unroll
+        for (int yy = 0; yy < 8; ++yy) ws[yy][u] = y[yy] >> 11;
+    }
+    // Eq. 2: row pass over u for each spatial row, level shift, clamp.
+#pragma unroll
+    for (int yy = 0; yy < 8; ++yy) {
+        int y[8];
+        idct8(ws[yy][0], ws[yy][1], ws[yy][2], ws[yy][3], ws[yy][4], ws[yy][5], ws[yy][6], ws[yy][7],
+              (1 << 17) + (128 << 18), y);
+        uint2 out;
+        out.x = pack_sat4(y[0] >> 18, y[1] >> 18, y[2] >> 18, y[3] >> 18);
+        out.y = pack_sat4(y[4] >> 18, y[5] >> 18, y[6] >> 18, y[7] >> 18);
+        *reinterpret_cast<uint2 *>(dst + yy * pitch) = out;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Colour conversion (Sec. 4.3, Alg. 2) in 16-bit fixed point with the
+// chroma offset and the rounding folded into one constant per channel:
+//   R = Y + ((91881 Cr - 11728000) >> 16)
+//   G = Y + ((-22554 Cb - 46802 Cr + 8910336) >> 16)
+//   B = Y + ((116130 Cb - 14831872) >> 16)
+// (91881 = round(1.402 * 2^16), 22554, 46802, 116130 likewise; the constant
+// terms are -c*128*2^16/2^16 + 2^15.)  Y is added before the shift as
+// Y * 2^16, which is exact.  Saturation happens in the byte pack.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ycc_rgb(int y, int cb, int cr, int &r, int &g, int &b)
+{
+    const int ys = y << 16;
+    r = (ys + cr * 91881 - 11728000) >> 16;
+    g = (ys - cb * 22554 - cr * 46802 + 8910336) >> 16;
+    b = (ys + cb * 116130 - 14831872) >> 16;
+}
+
+// Converts 8 pixels and writes 24 bytes to `out` (global).  `n` = pixels
+// inside the image (1..8); `vec` = the 8-byte vector path is allowed.
+__device__ __forceinline__ void cc_store8(const int Y[8], const int Cb[8], const int Cr[8],
+                                          uint8_t *out, int n, bool vec)
+{
+    int R[8], G[8], B[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ycc_rgb(Y[k], Cb[k], Cr[k], R[k], G[k], B[k]);
+    if (vec && n == 8) {
+        uint2 *o = reinterpret_cast<uint2 *>(out);
+        o[0] = make_uint2(pack_sat4(R[0], G[0], B[0], R[1]), pack_sat4(G[1], B[1], R[2], G[2]));
+        o[1] = make_uint2(pack_sat4(B[2], R[3], G[3], B[3]), pack_sat4(R[4], G[4], B[4], R[5]));
+        o[2] = make_uint2(pack_sat4(G[5], B[5], R[6], G[6]), pack_sat4(B[6], R[7], G[7], B[7]));
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (k < n) {
+                out[3 * k + 0] = static_cast<uint8_t>(min(max(R[k], 0), 255));
+                out[3 * k + 1] = static_cast<uint8_t>(min(max(G[k], 0), 255));
+                out[3 * k + 2] = static_cast<uint8_t>(min(max(B[k], 0), 255));
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ int byte_of(uint32_t w, int i) { return (w >> (8 * i)) & 0xff; }
+
+// Eight consecutive samples of a shared plane row starting at an 8-byte
+// aligned address.
+__device__ __forceinline__ void load8(const uint8_t *p, int v[8])
+{
+    const uint2 w = *reinterpret_cast<const uint2 *>(p);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { v[k] = byte_of(w.x, k); v[4 + k] = byte_of(w.y, k); }
+}
+
+// Six samples p[-1 .. 4] around four chroma centres starting at the 4-byte
+// aligned address p.
+__device__ __forceinline__ void load6(const uint8_t *p, int c[6])
+{
+    const uint32_t l = *reinterpret_cast<const uint32_t *>(p - 4);
+    const uint32_t m = *reinterpret_cast<const uint32_t *>(p);
+    const uint32_t r = *reinterpret_cast<const uint32_t *>(p + 4);
+    c[0] = byte_of(l, 3);
+    c[1] = byte_of(m, 0); c[2] = byte_of(m, 1); c[3] = byte_of(m, 2); c[4] = byte_of(m, 3);
+    c[5] = byte_of(r, 0);
+}
+
+// Alg. 1 (h2v1 triangular) for four centres c[1..4] with neighbours c[0], c[5].
+__device__ __forceinline__ void tri_h2v1(const int c[6], int o[8])
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        o[2 * k] = (3 * c[k + 1] + c[k] + 1) >> 2;
+        o[2 * k + 1] = (3 * c[k + 1] + c[k + 2] + 2) >> 2;
+    }
+}
+
+// h2v2 triangular: vertical 3:1 sums of the near and far rows, then the
+// horizontal 3:1 filter with one rounding (+8 / +7, >> 4).
+__device__ __forceinline__ void tri_h2v2(const int n[6], const int f[6], int o[8])
+{
+    int s[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s[k] = 3 * n[k] + f[k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        o[2 * k] = (3 * s[k + 1] + s[k] + 8) >> 4;
+        o[2 * k + 1] = (3 * s[k + 1] + s[k + 2] + 7) >> 4;
+    }
+}
+
+}  // namespace jdec

@@ -1,0 +1,78 @@
+// jdec_kernels.cu -- __global__ entry points of the GB300 back-end.
+//
+//   jdec_fused_kernel<HM, VM, FANCY>: one image; CTA b runs work item
+//     (strip = b % nstrips, chunk = b / nstrips).
+//
+// Variants: (HM, VM) = (1,1) 4:4:4, (2,1) 4:2:2, (2,2) 4:2:0; FANCY selects
+// the triangular filter of Alg. 1 (Sec. 4.2) over replication.
+#include <cuda_runtime.h>
+#include "jdec_work.cuh"
+#include "jdec_launch.h"
+
+namespace jdec {
+
+__device__ __forceinline__ uint8_t *align1024(uint8_t *p)
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    return reinterpret_cast<uint8_t *>((a + 1023) & ~static_cast<uintptr_t>(1023));
+}
+
+template <int HM, int VM, bool FANCY>
+__global__ void __launch_bounds__(kThreads) jdec_fused_kernel(const __grid_constant__ DecodeParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = align1024(smem_raw);
+    const SmemLayout L = smem_layout(HM, VM, FANCY, p.img.wt);
+    int *qs = reinterpret_cast<int *>(smem + L.off_q);
+    for (int i = threadIdx.x; i < 192; i += blockDim.x) qs[i] = p.img.q[i >> 6][i & 63];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(smem_u32(smem + L.off_bar + 8 * s), 1);
+        fence_barrier_init();
+        for (int c = 0; c < 3; ++c) tma_prefetch_map(&p.tmap[c]);
+    }
+    __syncthreads();
+    PipeState ps{0u};
+    const int strip = blockIdx.x % p.img.nstrips;
+    const int chunk = blockIdx.x / p.img.nstrips;
+    run_work<HM, VM, FANCY>(p.tmap, p.img, strip, chunk, smem, ps, p.err);
+}
+
+template <int HM, int VM, bool FANCY>
+static cudaError_t launch_variant(const DecodeParams &p, int grid, int smem, cudaStream_t s)
+{
+    auto k = jdec_fused_kernel<HM, VM, FANCY>;
+    static int configured_smem = 0;
+    if (smem > configured_smem) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured_smem = smem;
+    }
+    k<<<grid, kThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused(int hm, int vm, bool fancy, const DecodeParams &p, int grid, int smem, cudaStream_t s)
+{
+    if (hm == 1) return launch_variant<1, 1, false>(p, grid, smem, s);
+    if (vm == 1) return fancy ? launch_variant<2, 1, true>(p, grid, smem, s) : launch_variant<2, 1, false>(p, grid, smem, s);
+    return fancy ? launch_variant<2, 2, true>(p, grid, smem, s) : launch_variant<2, 2, false>(p, grid, smem, s);
+}
+
+template <int HM, int VM, bool FANCY>
+static int occupancy_variant(int smem)
+{
+    int n = 0;
+    auto k = jdec_fused_kernel<HM, VM, FANCY>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+int fused_occupancy(int hm, int vm, bool fancy, int smem)
+{
+    if (hm == 1) return occupancy_variant<1, 1, false>(smem);
+    if (vm == 1) return fancy ? occupancy_variant<2, 1, true>(smem) : occupancy_variant<2, 1, false>(smem);
+    return fancy ? occupancy_variant<2, 2, true>(smem) : occupancy_variant<2, 2, false>(smem);
+}
+
+}  // namespace jdec

@@ -1,0 +1,14 @@
+// jdec_launch.h -- host-side launch interface of the kernels TU.
+#pragma once
+
+#include <cuda_runtime.h>
+#include "jdec_common.h"
+
+namespace jdec {
+
+constexpr int kThreads = 64;   // threads per CTA of the fused kernel
+
+cudaError_t launch_fused(int hm, int vm, bool fancy, const DecodeParams &p, int grid, int smem, cudaStream_t s);
+int fused_occupancy(int hm, int vm, bool fancy, int smem);
+
+}  // namespace jdec

@@ -1,0 +1,247 @@
+// jdec_runtime.cu -- host runtime: strip-width autotuner and its table,
+// the host-buffer path (row bands whose copies overlap decoding, the
+// pipelined execution of Sec. 4.5 with the entropy decoder replaced by the
+// host->device copy), and context teardown.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "jdec_launch.h"
+#include "jdec_runtime.h"
+
+namespace jdec {
+
+int variant_of(const Geometry &g)
+{
+    if (g.hm == 1) return 0;
+    if (g.vm == 1) return g.fancy ? 2 : 1;
+    return g.fancy ? 4 : 3;
+}
+
+int size_class_of(const Geometry &g)
+{
+    const long mcus = static_cast<long>(g.mcus_x) * g.mcus_y;
+    int c = 0;
+    while ((1L << (c + 1)) <= mcus && c < 40) ++c;
+    return c / 2;   // buckets of 4x in MCU count
+}
+
+int tuned_wt(jdec_ctx *ctx, const Geometry &g)
+{
+    const int v = variant_of(g), sc = size_class_of(g);
+    for (int i = 0; i < ctx->n_tune; ++i)
+        if (ctx->tune[i].variant == v && ctx->tune[i].size_class == sc) return ctx->tune[i].wt;
+    return 0;
+}
+
+static const char *tune_path(jdec_ctx *ctx)
+{
+    if (ctx->opt.tune_file && ctx->opt.tune_file[0]) return ctx->opt.tune_file;
+    const char *e = getenv("JDEC_TUNE_FILE");
+    return (e && e[0]) ? e : nullptr;
+}
+
+// Table format: {"gpu": "<name>", "sms": N, "entries": [[variant, size_class, wt], ...]}
+void load_tune_table(jdec_ctx *ctx)
+{
+    const char *path = tune_path(ctx);
+    if (!path) return;
+    FILE *f = fopen(path, "rb");
+    if (!f) return;
+    std::vector<char> buf(1 << 16);
+    const size_t n = fread(buf.data(), 1, buf.size() - 1, f);
+    fclose(f);
+    buf[n] = 0;
+    const char *p = strstr(buf.data(), "\"sms\"");
+    if (!p) return;
+    int sms = 0;
+    if (sscanf(strchr(p, ':') + 1, "%d", &sms) != 1 || sms != ctx->sms) return;   // other GPU: ignore
+    p = strstr(buf.data(), "\"entries\"");
+    if (!p) return;
+    p = strchr(p, '[');
+    if (!p) return;
+    ++p;
+    while (ctx->n_tune < 64) {
+        const char *q = strchr(p, '[');
+        if (!q) break;
+        int v, sc, wt;
+        if (sscanf(q, "[%d , %d , %d]", &v, &sc, &wt) != 3 && sscanf(q, "[%d,%d,%d]", &v, &sc, &wt) != 3) break;
+        if (wt >= 1 && wt <= kMaxWT) ctx->tune[ctx->n_tune++] = TuneEntry{v, sc, wt};
+        p = strchr(q, ']');
+        if (!p) break;
+        ++p;
+    }
+}
+
+void save_tune_table(jdec_ctx *ctx)
+{
+    const char *path = tune_path(ctx);
+    if (!path) return;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess) return;
+    FILE *f = fopen(path, "wb");
+    if (!f) return;
+    fprintf(f, "{\"gpu\": \"%s\", \"sms\": %d, \"entries\": [", prop.name, ctx->sms);
+    for (int i = 0; i < ctx->n_tune; ++i)
+        fprintf(f, "%s[%d, %d, %d]", i ? ", " : "", ctx->tune[i].variant, ctx->tune[i].size_class, ctx->tune[i].wt);
+    fprintf(f, "]}\n");
+    fclose(f);
+}
+
+// Times the candidate strip widths on this image (the output is rewritten
+// with identical bytes) and records the fastest for its variant and size
+// class.  Runs once per (variant, size class); synchronises the stream.
+void autotune_shape(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cudaStream_t s)
+{
+    if (tuned_wt(ctx, g) > 0 || ctx->n_tune >= 64) return;
+    static const int cand[] = {4, 6, 8, 10, 12, 14, 16, 20, 24, 32};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return; }
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int wt : cand) {
+        if (wt > 2 * g.mcus_x && wt != cand[0]) break;
+        float tot = 0.f;
+        bool ok = true;
+        for (int rep = 0; rep < 4 && ok; ++rep) {
+            cudaEventRecord(e0, s);
+            ok = launch_image(ctx, img, g, s, wt) == JDEC_OK;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tot += ms;   // first launch warms the caches
+        }
+        if (ok && tot < best_ms) { best_ms = tot; best = wt; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best > 0) {
+        ctx->tune[ctx->n_tune++] = TuneEntry{variant_of(g), size_class_of(g), best};
+        save_tune_table(ctx);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-buffer path: copy -> decode -> copy back in row bands.
+// ---------------------------------------------------------------------------
+struct HostStreams {
+    cudaStream_t h2d = nullptr, comp = nullptr, d2h = nullptr;
+};
+
+static HostStreams &host_streams(jdec_ctx *ctx)
+{
+    static thread_local HostStreams hs[16];
+    HostStreams &h = hs[ctx->device & 15];
+    if (!h.h2d) {
+        cudaStreamCreateWithFlags(&h.h2d, cudaStreamNonBlocking);
+        cudaStreamCreateWithFlags(&h.comp, cudaStreamNonBlocking);
+        cudaStreamCreateWithFlags(&h.d2h, cudaStreamNonBlocking);
+    }
+    return h;
+}
+
+static cudaEvent_t band_event(jdec_ctx *ctx, int i)
+{
+    while (ctx->n_band_ev <= i && ctx->n_band_ev < 64) {
+        if (cudaEventCreateWithFlags(&ctx->band_ev[ctx->n_band_ev], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        ctx->n_band_ev++;
+    }
+    return i < ctx->n_band_ev ? ctx->band_ev[i] : nullptr;
+}
+
+jdec_status decode_host_banded(jdec_ctx *ctx, const jdec_image *himg, const Geometry &g, cudaStream_t s)
+{
+    // device staging: three planes (256-byte aligned) + dense RGB
+    size_t off[3], tot = 0;
+    for (int c = 0; c < 3; ++c) {
+        off[c] = tot;
+        tot += (static_cast<size_t>(himg->blocks_w[c]) * himg->blocks_h[c] * 128 + 255) & ~static_cast<size_t>(255);
+    }
+    jdec_status st = ensure_buffer(ctx, &ctx->h_coef, &ctx->h_coef_cap, tot);
+    if (st != JDEC_OK) return st;
+    const size_t rgb_pitch = 3 * static_cast<size_t>(g.W);
+    st = ensure_buffer(ctx, &ctx->h_rgb, &ctx->h_rgb_cap, rgb_pitch * g.H);
+    if (st != JDEC_OK) return st;
+
+    jdec_image dimg = *himg;
+    for (int c = 0; c < 3; ++c) dimg.coef[c] = reinterpret_cast<const int16_t *>(static_cast<uint8_t *>(ctx->h_coef) + off[c]);
+    dimg.rgb = static_cast<uint8_t *>(ctx->h_rgb);
+    dimg.rgb_pitch = static_cast<int64_t>(rgb_pitch);
+
+    HostStreams &hs = host_streams(ctx);
+    const int nb = std::min(8, g.mcus_y);
+    // bands: event indices [0, nb) after H2D of band k, [nb, 2nb) after decode
+    cudaEvent_t fork = band_event(ctx, 2 * nb);
+    cudaEvent_t join = band_event(ctx, 2 * nb + 1);
+    if (!fork || !join) return JDEC_ECUDA;
+    if (cudaEventRecord(fork, s) != cudaSuccess) return JDEC_ECUDA;
+    cudaStreamWaitEvent(hs.h2d, fork, 0);
+    cudaStreamWaitEvent(hs.comp, fork, 0);
+    cudaStreamWaitEvent(hs.d2h, fork, 0);
+    const int lookahead = (g.fancy && g.vm == 2) ? 1 : 0;
+    for (int k = 0; k < nb; ++k) {
+        const int r0 = static_cast<int>(static_cast<long>(g.mcus_y) * k / nb);
+        const int r1 = static_cast<int>(static_cast<long>(g.mcus_y) * (k + 1) / nb);
+        for (int c = 0; c < 3; ++c) {
+            const int v = c ? 1 : g.vm;
+            const size_t row_bytes = static_cast<size_t>(himg->blocks_w[c]) * 128;
+            const size_t o = static_cast<size_t>(r0) * v * row_bytes;
+            const size_t n = static_cast<size_t>(r1 - r0) * v * row_bytes;
+            if (cudaMemcpyAsync(static_cast<uint8_t *>(ctx->h_coef) + off[c] + o,
+                                reinterpret_cast<const uint8_t *>(himg->coef[c]) + o, n, cudaMemcpyHostToDevice,
+                                hs.h2d) != cudaSuccess)
+                return JDEC_ECUDA;
+        }
+        cudaEventRecord(band_event(ctx, k), hs.h2d);
+        // decode band k - lookahead once its chroma look-ahead row has arrived
+        const int kd = k - lookahead;
+        if (kd >= 0) {
+            cudaStreamWaitEvent(hs.comp, band_event(ctx, k), 0);
+            const int d0 = static_cast<int>(static_cast<long>(g.mcus_y) * kd / nb);
+            const int d1 = static_cast<int>(static_cast<long>(g.mcus_y) * (kd + 1) / nb);
+            st = launch_rows(ctx, &dimg, g, hs.comp, d0, d1, 0);
+            if (st != JDEC_OK) return st;
+            cudaEventRecord(band_event(ctx, nb + kd), hs.comp);
+        }
+    }
+    if (lookahead) {
+        const int kd = nb - 1;
+        const int d0 = static_cast<int>(static_cast<long>(g.mcus_y) * kd / nb);
+        st = launch_rows(ctx, &dimg, g, hs.comp, d0, g.mcus_y, 0);
+        if (st != JDEC_OK) return st;
+        cudaEventRecord(band_event(ctx, nb + kd), hs.comp);
+    }
+    const int mcu_h = 8 * g.vm;
+    for (int k = 0; k < nb; ++k) {
+        const int r0 = static_cast<int>(static_cast<long>(g.mcus_y) * k / nb);
+        const int r1 = static_cast<int>(static_cast<long>(g.mcus_y) * (k + 1) / nb);
+        const int y0 = r0 * mcu_h, y1 = std::min(g.H, r1 * mcu_h);
+        if (y1 <= y0) continue;
+        cudaStreamWaitEvent(hs.d2h, band_event(ctx, nb + k), 0);
+        if (cudaMemcpy2DAsync(himg->rgb + static_cast<int64_t>(y0) * himg->rgb_pitch, himg->rgb_pitch,
+                              static_cast<uint8_t *>(ctx->h_rgb) + y0 * rgb_pitch, rgb_pitch, rgb_pitch, y1 - y0,
+                              cudaMemcpyDeviceToHost, hs.d2h) != cudaSuccess)
+            return JDEC_ECUDA;
+    }
+    if (cudaEventRecord(join, hs.d2h) != cudaSuccess) return JDEC_ECUDA;
+    if (cudaStreamWaitEvent(s, join, 0) != cudaSuccess) return JDEC_ECUDA;
+    return JDEC_OK;
+}
+
+void release_runtime(jdec_ctx *ctx)
+{
+    if (ctx->h_coef) cudaFree(ctx->h_coef);
+    if (ctx->h_rgb) cudaFree(ctx->h_rgb);
+    ctx->h_coef = ctx->h_rgb = nullptr;
+    for (int i = 0; i < ctx->n_band_ev; ++i) cudaEventDestroy(ctx->band_ev[i]);
+    ctx->n_band_ev = 0;
+    release_batch(ctx);
+}
+
+}  // namespace jdec

@@ -1,0 +1,87 @@
+// jdec_runtime.h -- context state and host-runtime internals of the C ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/jdec.h"
+#include "jdec_common.h"
+
+namespace jdec {
+
+struct Geometry {
+    int hm, vm;
+    bool fancy;
+    int W, H;
+    int mcus_x, mcus_y;
+    int cw, ch;
+    int64_t coef_bytes, rgb_bytes;
+};
+
+// Autotuned strip width per (variant, size class).
+struct TuneEntry {
+    int variant;     // 0: 4:4:4, 1: 4:2:2 replicate, 2: 4:2:2 fancy, 3: 4:2:0 replicate, 4: 4:2:0 fancy
+    int size_class;  // log2 of the MCU count, bucketed
+    int wt;
+};
+
+struct BatchState;
+
+}  // namespace jdec
+
+struct jdec_ctx {
+    jdec_options opt;
+    int device = 0;
+    int sms = 0;
+    int *d_err = nullptr;
+    size_t owned_bytes = 0;
+    long launches = 0;
+    // occupancy cache
+    int occ_key[32][2];
+    int occ_val[32];
+    int n_occ = 0;
+    // tune table
+    jdec::TuneEntry tune[64];
+    int n_tune = 0;
+    // host-buffer path: device staging
+    void *h_coef = nullptr;
+    size_t h_coef_cap = 0;
+    void *h_rgb = nullptr;
+    size_t h_rgb_cap = 0;
+    cudaEvent_t band_ev[64];
+    int n_band_ev = 0;
+    // batched path
+    jdec::BatchState *batch = nullptr;
+};
+
+namespace jdec {
+
+const char *status_str(jdec_status s);
+bool encode_plane_map(CUtensorMap *m, const int16_t *base, int bw, int bh, int box_w, int box_h);
+jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers);
+void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int *wt, int *rpc, int *nchunks,
+                int *smem);
+void fill_desc(ImageDesc *d, const jdec_image *img, const Geometry &g, int wt, int rpc, int nchunks);
+bool encode_maps(CUtensorMap maps[3], const jdec_image *img, const Geometry &g, int wt);
+jdec_status launch_rows(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cudaStream_t s, int row0,
+                        int row1, int force_wt);
+jdec_status launch_image(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cudaStream_t s, int force_wt);
+int occupancy_cached(jdec_ctx *ctx, int hm, int vm, bool fancy, int smem);
+jdec_status ensure_buffer(jdec_ctx *ctx, void **buf, size_t *cap, size_t need);
+
+int variant_of(const Geometry &g);
+int size_class_of(const Geometry &g);
+int tuned_wt(jdec_ctx *ctx, const Geometry &g);
+void load_tune_table(jdec_ctx *ctx);
+void save_tune_table(jdec_ctx *ctx);
+void autotune_shape(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cudaStream_t s);
+
+jdec_status decode_host_banded(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cudaStream_t s);
+jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStream_t s);
+void release_runtime(jdec_ctx *ctx);
+void release_batch(jdec_ctx *ctx);
+
+}  // namespace jdec

@@ -58,5 +58,5 @@ def test_decoded_image_psnr(orc):
     img = synth.make_image(128, 96, "420", 80, kind="gradient", sigma=2)
     info, planes = orc.jpeg_decode_coefs(synth.encode_jfif(img))
     rgb = orc.backend_decode(128, 96, info["h_samp"], info["v_samp"], planes, info["qtabs"], True).astype(float)
-    src = np.clip(np.rint(synth._Content(128, 96, img.meta["seed"], "gradient", 2).rgb(0, 96, 0)), 0, 255)
+    src = np.clip(np.rint(synth.render_rgb(128, 96, img.meta["seed"], "gradient", 2)), 0, 255)
     assert 10 * np.log10(255 ** 2 / np.mean((rgb - src) ** 2)) > 30
