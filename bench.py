@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 JPEG decode back-end (one JSON line on stdout).
+
+Workload (one "step"): the three 8192 x 8192 synthetic images of the
+full-size configuration -- 4:4:4, 4:2:2 (H2V1) and 4:2:0 (H2V2), quality 90,
+textured content, triangular upsampling -- each decoded by one launch of the
+fused kernel through the C ABI (dequant + IDCT + upsample + YCbCr->RGB).
+Inputs are int16 coefficient planes already resident in HBM; 1.48 GB move per
+step, far larger than L2, so no flush is needed between steps.
+
+  value       MPix/s over the timed steps (device-timed, CUDA events), summed
+              over ranks (each rank decodes its own replica: weak scaling)
+  e2e         the same metric through jdec_decode_host: pinned host planes in,
+              pinned host RGB out, copies inside the timed region
+  roofline    algorithmic bytes (128 B per coefficient block + 3 B per pixel)
+              per launch / mean launch time, against the measured HBM peak
+  cpu_baseline  the CPU oracle on the host cores, on a bounded sample
+
+``--impl reference`` times the CPU oracle (the reference arm of this
+comparison) on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MPix/s for dequant+IDCT+upsample+YCC→RGB, % HBM peak, batched vs plain, p99 ms"
+SIDE = 8192
+QUALITY = 90
+VARIANTS = ["444", "422", "420"]
+SEED = 13115304 + 2000
+WORKLOAD = "8192x8192 q90 texture, 4:4:4 + 4:2:2 + 4:2:0, triangular upsampling (3 images per step)"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(size=(SIDE, SIDE), variants=VARIANTS):
+    from paper_1311_5304_gb300 import synth
+    return [synth.make_image(size[0], size[1], s, QUALITY, seed=SEED, kind="texture", sigma=4.0, cover=0.85,
+                             fancy=True) for s in variants]
+
+
+def alg_bytes(img) -> int:
+    return img.coef_bytes() + img.rgb_bytes()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1311_5304_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "fused_kernel_8192_ncu.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
+    m_tr = re.search(r"dram_bytes_per_step:\s*([0-9.eE+]+)", txt)
+    if not m_sha or not m_tr or m_sha.group(1) != kernel_source_sha():
+        return None
+    return float(m_tr.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(parts)
+            except ValueError:
+                pass
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_1311_5304_gb300 import jdec
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    t_gen = time.time()
+    imgs = make_workload(args.size, args.variants)
+    log(f"[bench] workload generated in {time.time() - t_gen:.1f}s")
+    planes = [[torch.from_numpy(np.ascontiguousarray(p)).to(dev) for p in im.planes] for im in imgs]
+    rgbs = [torch.empty((im.height, im.width, 3), dtype=torch.uint8, device=dev) for im in imgs]
+    ctx = jdec.Context(device=local)
+    keep = []
+    descs = [jdec.make_image(im.width, im.height, (im.h_samp, im.v_samp), planes[i], im.qtabs, rgbs[i],
+                             fancy=True, keep=keep) for i, im in enumerate(imgs)]
+    stream = torch.cuda.current_stream(dev)
+    px_step = sum(im.width * im.height for im in imgs)
+    bytes_v = [alg_bytes(im) for im in imgs]
+
+    def step(evs=None):
+        for i, d in enumerate(descs):
+            if evs is not None:
+                evs[i][0].record(stream)
+            ctx.decode_coeffs(d, stream)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync(stream)
+
+    K = args.steps
+    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in descs]
+           for _ in range(K)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    t_start.record(stream)
+    for k in range(K):
+        step(evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ctx.sync(stream)
+    elapsed_ms = t_start.elapsed_time(t_end)
+    per_var_ms = [statistics.mean(evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(K))
+                  for i in range(len(descs))]
+    if ws > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = px_step * K * ws / (elapsed_ms / 1e3) / 1e6
+
+    # ---- end to end through the host-buffer entry point ----
+    e2e = None
+    if not args.no_e2e:
+        host_planes = [[torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p in im.planes] for im in imgs]
+        host_rgb = [torch.empty((im.height, im.width, 3), dtype=torch.uint8).pin_memory() for im in imgs]
+        hdescs = [jdec.make_image(im.width, im.height, (im.h_samp, im.v_samp),
+                                  [hp.numpy() for hp in host_planes[i]], im.qtabs, host_rgb[i].numpy(),
+                                  fancy=True, keep=keep, host=True) for i, im in enumerate(imgs)]
+        for d in hdescs:
+            ctx.decode_host(d, stream)
+        ctx.sync(stream)
+        Ke = max(1, min(args.e2e_steps, K))
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(Ke):
+            for d in hdescs:
+                ctx.decode_host(d, stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        e_ms = a.elapsed_time(b)
+        if ws > 1:
+            t = torch.tensor([e_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e_ms = float(t.item())
+        ctx.sync(stream)
+        e2e = {"value": round(px_step * Ke * ws / (e_ms / 1e3) / 1e6, 1), "unit": "MPix/s",
+               "h2d_bytes_per_step": int(sum(im.coef_bytes() for im in imgs)),
+               "d2h_bytes_per_step": int(sum(im.rgb_bytes() for im in imgs)),
+               "steps": Ke, "ms_per_step": round(e_ms / Ke, 3),
+               "api": "jdec_decode_host (pinned host buffers, banded H2D/decode/D2H)"}
+
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    tot_bytes = sum(bytes_v)
+    tot_ms = sum(per_var_ms)
+    achieved = tot_bytes / (tot_ms / 1e3) / 1e9
+    traffic = profiled_traffic()
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+                "kernel": "jdec_fused_kernel (3 variants per step)",
+                "algorithmic_bytes_per_step": tot_bytes,
+                "by_variant": {v: {"bytes": bytes_v[i], "ms": round(per_var_ms[i], 4),
+                                   "gbs": round(bytes_v[i] / (per_var_ms[i] / 1e3) / 1e9, 1),
+                                   "frac": round(bytes_v[i] / (per_var_ms[i] / 1e3) / 1e9 / peak, 4),
+                                   "gpix_s": round(imgs[i].width * imgs[i].height / (per_var_ms[i] / 1e3) / 1e9, 1)}
+                               for i, v in enumerate(args.variants)}}
+
+    workload = WORKLOAD if (args.size == (SIDE, SIDE) and args.variants == VARIANTS) else \
+        f"{args.size[0]}x{args.size[1]} q90 texture, {'+'.join(args.variants)}, triangular upsampling"
+    out = {"metric": METRIC, "value": round(value, 1), "unit": "MPix/s", "n_gpus": ws, "steps": K,
+           "warmup": args.warmup, "ms_per_step": round(elapsed_ms / K, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded)",
+           "config": {"workload": workload, "images_per_step": len(imgs), "mpix_per_step": px_step / 1e6,
+                      "seed": SEED, "l2": f"inputs larger than L2 ({tot_bytes / 1e9:.2f} GB moved per step)",
+                      "parallelism": f"replicas x{ws}"},
+           "e2e": e2e, "roofline": roofline, "clocks": clocks, "gpu_launches": len(descs) * K}
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(imgs, args.cpu_seconds)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    ctx.close()
+    return out
+
+
+def cpu_baseline(imgs, seconds):
+    """The oracle (as it stands) on the host cores: whole 8192^2 images of the
+    step, decoded until `seconds` of wall time have passed."""
+    import oracle
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    done_px, t0, n = 0, time.time(), 0
+    while True:
+        im = imgs[n % len(imgs)]
+        oracle.backend_decode(im.width, im.height, im.h_samp, im.v_samp, im.planes, im.qtabs, True, threads=threads)
+        done_px += im.width * im.height
+        n += 1
+        if time.time() - t0 >= seconds and n >= len(imgs):
+            break
+    dt = time.time() - t0
+    return {"value": round(done_px / dt / 1e6, 2), "unit": "MPix/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n} whole 8192x8192 images of the step (cycling 4:4:4/4:2:2/4:2:0), {dt:.1f}s wall"}
+
+
+def run_reference(args, ws, rank):
+    """The CPU oracle timed as the reference arm (rank 0 only)."""
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    imgs = make_workload()
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    # each step: one band of `band` rows of each of the three images, the band
+    # height chosen so that the whole run stays near one minute of wall time
+    from paper_1311_5304_gb300 import synth
+    band = 1024
+
+    def band_img(im):
+        hs, vs, mx, my = synth.geometry(im.width, band, im.sampling)
+        planes = [p[:my * vs[c]] for c, p in enumerate(im.planes)]
+        return im.width, band, im.h_samp, im.v_samp, planes, im.qtabs
+
+    bands = [band_img(im) for im in imgs]
+    t0 = time.time()
+    for (w, h, hs, vs, planes, qt) in bands:
+        oracle.backend_decode(w, h, hs, vs, planes, qt, True, threads=threads)
+    t_full = time.time() - t0
+    budget = 60.0 / max(1, args.steps + args.warmup)
+    band = int(max(16, min(1024, 1024 * budget / max(t_full, 1e-6))) // 16 * 16)
+    bands = [band_img(im) for im in imgs]
+    px = sum(b[0] * b[1] for b in bands)
+
+    def step():
+        for (w, h, hs, vs, planes, qt) in bands:
+            oracle.backend_decode(w, h, hs, vs, planes, qt, True, threads=threads)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.time()
+    for _ in range(args.steps):
+        step()
+    dt = time.time() - t0
+    value = px * args.steps / dt / 1e6
+    return {"metric": METRIC, "value": round(value, 2), "unit": "MPix/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded)",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "images_per_step": len(imgs), "mpix_per_step": px / 1e6,
+                       "sample": f"rows 0..{band - 1} of each of the three 8192-wide images per step"},
+            "cpu_baseline": {"value": round(value, 2), "unit": "MPix/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{args.steps} steps of 3 x 8192x{band} bands"},
+            "e2e": {"value": round(value, 2), "unit": "MPix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", default=f"{SIDE}x{SIDE}", help="WxH of every image of the step")
+    ap.add_argument("--variants", default=",".join(VARIANTS), help="samplings decoded per step")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    args.size = tuple(int(v) for v in args.size.lower().split("x"))
+    args.variants = [v for v in args.variants.split(",") if v]
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+    else:
+        from paper_1311_5304_gb300 import build as jbuild
+        jbuild.build()
+        out = run_ours(args, ws, rank, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -113,15 +113,25 @@ jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers)
     return JDEC_OK;
 }
 
+// Default strip width: as many coefficient blocks per MCU row as IDCT threads
+// (96 for 4:4:4, 64 otherwise), so every IDCT thread transforms one block
+// per job.
+int default_wt(const Geometry &g)
+{
+    if (g.hm == 1) return 32;                 // 3 blocks per MCU
+    if (g.vm == 1) return g.fancy ? 15 : 16;  // 4 blocks per MCU (+ 4 halo blocks)
+    return 10;                                // 6 blocks per MCU (+ 4 halo blocks)
+}
+
 // Strip width (MCUs) and chunk height (MCU rows) for `nrows` MCU rows of an
 // image: enough work items to fill every SM at the kernel's occupancy.
 void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int *wt, int *rpc, int *nchunks,
                 int *smem)
 {
     int w = force_wt > 0 ? force_wt : tuned_wt(ctx, g);
-    if (w <= 0) w = (g.hm == 1) ? 16 : (g.vm == 1 ? 12 : 8);
+    if (w <= 0) w = default_wt(g);
     w = std::max(1, std::min(w, kMaxWT));
-    const SmemLayout L = smem_layout(g.hm, g.vm, g.fancy, w);
+    const SmemLayout L = smem_layout(g.hm, g.vm, g.fancy, w, default_slots(g.hm, g.vm, g.fancy));
     const int occ = occupancy_cached(ctx, g.hm, g.vm, g.fancy, L.total);
     const int nstrips = (g.mcus_x + w - 1) / w;
     const long target = static_cast<long>(occ) * ctx->sms;
@@ -150,6 +160,7 @@ void fill_desc(ImageDesc *d, const jdec_image *img, const Geometry &g, int wt, i
     d->nchunks = nchunks;
     d->row0 = 0;
     d->row1 = g.mcus_y;
+    d->nslot = default_slots(g.hm, g.vm, g.fancy);
     d->aligned8 = ((reinterpret_cast<uintptr_t>(img->rgb) | static_cast<uintptr_t>(img->rgb_pitch)) & 7) == 0;
     for (int c = 0; c < 3; ++c)
         for (int k = 0; k < 64; ++k) d->q[c][k] = img->qtab[c][k];

@@ -29,7 +29,7 @@ struct ImageDesc {
     int32_t nchunks;
     int32_t aligned8;       // rgb and pitch are 8-byte aligned
     int32_t row0, row1;     // MCU rows [row0, row1) covered by the launch
-    int32_t pad_;
+    int32_t nslot;          // chroma slots of the shared-memory ring (2 or 4)
     int32_t q[3][64];       // dequantisation tables, natural order
 };
 
@@ -40,16 +40,28 @@ struct DecodeParams {
     int *err;               // device error word
 };
 
+// Threads of a CTA: IDCT warps (producers) + upsample/colour warps (consumers).
+constexpr int kWarps = 4;
+constexpr int kCtaThreads = 32 * kWarps;
+__host__ __device__ inline int idct_warps(int hm) { return hm == 1 ? 3 : 2; }
+
 // Shared-memory carve-up of one CTA; identical on host and device.
+//   stages : kStages coefficient tiles written by TMA (1024-aligned regions)
+//   y      : 2 luma sample planes (double buffer), (8*VM) x (8*HM*wt) bytes
+//   c      : nslot chroma slots (4 for 4:2:0 triangular filtering, else 2),
+//            each 2 components x 8 rows x lc bytes
 struct SmemLayout {
     int ny, nc;             // Y blocks per step, chroma blocks per component per step
-    int lc;                 // chroma samples per plane row (with halo blocks)
-    int nslot;              // chroma block rows kept (3 for vertical triangular filtering)
-    int stage_y, stage_c;   // byte offsets of the chroma regions inside a stage
-    int stage_bytes;        // one coefficient stage (1024-aligned regions)
+    int lc;                 // chroma samples per slot row (with halo blocks)
+    int stage_y, stage_c;   // byte offsets of the regions inside a stage
+    int cbytes;             // bytes of one chroma component region of a stage
+    int stage_bytes;        // one coefficient stage
     int off_stage;          // offset of stage 0
-    int off_y;              // Y sample plane, (8*VM) x (8*HM*wt)
-    int off_c;              // chroma sample planes, 2 x nslot x 8 x lc
+    int ypitch, ybytes;     // luma plane pitch and size
+    int off_y;              // luma planes
+    int nslot;              // chroma slots
+    int slot_bytes;         // one chroma slot (both components)
+    int off_c;              // chroma slots
     int off_q;              // dequantisation tables, int32 [3][64]
     int off_bar;            // mbarriers, one per stage
     int off_flag;           // CTA-wide flags
@@ -58,23 +70,29 @@ struct SmemLayout {
 
 __host__ __device__ inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline SmemLayout smem_layout(int hm, int vm, bool fancy, int wt)
+__host__ __device__ inline int default_slots(int hm, int vm, bool fancy) { return (fancy && hm == 2 && vm == 2) ? 4 : 2; }
+
+__host__ __device__ inline SmemLayout smem_layout(int hm, int vm, bool fancy, int wt, int nslot)
 {
     SmemLayout L;
     const int halo = (fancy && hm == 2) ? 1 : 0;
     L.ny = hm * vm * wt;
     L.nc = wt + 2 * halo;
-    L.lc = 8 * L.nc;
-    L.nslot = (fancy && hm == 2 && vm == 2) ? 3 : 1;
+    L.lc = round_up(8 * L.nc, 16);
     L.stage_y = 0;
     L.stage_c = round_up(L.ny * 128, 1024);
-    L.stage_bytes = L.stage_c + 2 * round_up(L.nc * 128, 1024);
+    L.cbytes = round_up(L.nc * 128, 1024);
+    L.stage_bytes = L.stage_c + 2 * L.cbytes;
     L.off_stage = 0;
     int off = kStages * L.stage_bytes;
+    L.ypitch = 8 * hm * wt;
+    L.ybytes = round_up(8 * vm * L.ypitch, 16);
     L.off_y = off;
-    off += round_up(8 * vm * 8 * hm * wt, 16);
+    off += 2 * L.ybytes;
+    L.nslot = nslot;
+    L.slot_bytes = 2 * 8 * L.lc;
     L.off_c = off;
-    off += round_up(2 * L.nslot * 8 * L.lc, 16);
+    off += nslot * L.slot_bytes;
     L.off_q = off;
     off += 3 * 64 * 4;
     L.off_bar = off;

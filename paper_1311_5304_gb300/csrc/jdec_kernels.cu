@@ -18,23 +18,24 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p)
 }
 
 template <int HM, int VM, bool FANCY>
-__global__ void __launch_bounds__(kThreads) jdec_fused_kernel(const __grid_constant__ DecodeParams p)
+__global__ void __launch_bounds__(kCtaThreads) jdec_fused_kernel(const __grid_constant__ DecodeParams p)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
-    const SmemLayout L = smem_layout(HM, VM, FANCY, p.img.wt);
+    const SmemLayout L = smem_layout(HM, VM, FANCY, p.img.wt, p.img.nslot);
     int *qs = reinterpret_cast<int *>(smem + L.off_q);
     for (int i = threadIdx.x; i < 192; i += blockDim.x) qs[i] = p.img.q[i >> 6][i & 63];
     if (threadIdx.x == 0) {
+        *reinterpret_cast<volatile int *>(smem + L.off_flag) = 0;
         for (int s = 0; s < kStages; ++s) mbar_init(smem_u32(smem + L.off_bar + 8 * s), 1);
         fence_barrier_init();
         for (int c = 0; c < 3; ++c) tma_prefetch_map(&p.tmap[c]);
     }
     __syncthreads();
-    PipeState ps{0u};
+    PipeState ps{0u, 0};
     const int strip = blockIdx.x % p.img.nstrips;
     const int chunk = blockIdx.x / p.img.nstrips;
-    run_work<HM, VM, FANCY>(p.tmap, p.img, strip, chunk, smem, ps, p.err);
+    run_work<HM, VM, FANCY>(p.tmap, p.img, strip, chunk, smem, ps, p.err, true);
 }
 
 template <int HM, int VM, bool FANCY>
@@ -47,7 +48,7 @@ static cudaError_t launch_variant(const DecodeParams &p, int grid, int smem, cud
         if (e != cudaSuccess) return e;
         configured_smem = smem;
     }
-    k<<<grid, kThreads, smem, s>>>(p);
+    k<<<grid, kCtaThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -64,7 +65,7 @@ static int occupancy_variant(int smem)
     int n = 0;
     auto k = jdec_fused_kernel<HM, VM, FANCY>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads, smem) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kCtaThreads, smem) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }
 

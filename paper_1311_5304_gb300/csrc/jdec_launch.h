@@ -6,8 +6,6 @@
 
 namespace jdec {
 
-constexpr int kThreads = 64;   // threads per CTA of the fused kernel
-
 cudaError_t launch_fused(int hm, int vm, bool fancy, const DecodeParams &p, int grid, int smem, cudaStream_t s);
 int fused_occupancy(int hm, int vm, bool fancy, int smem);
 

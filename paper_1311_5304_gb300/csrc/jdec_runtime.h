@@ -73,6 +73,7 @@ int occupancy_cached(jdec_ctx *ctx, int hm, int vm, bool fancy, int smem);
 jdec_status ensure_buffer(jdec_ctx *ctx, void **buf, size_t *cap, size_t need);
 
 int variant_of(const Geometry &g);
+int default_wt(const Geometry &g);
 int size_class_of(const Geometry &g);
 int tuned_wt(jdec_ctx *ctx, const Geometry &g);
 void load_tune_table(jdec_ctx *ctx);
