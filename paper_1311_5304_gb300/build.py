@@ -37,8 +37,14 @@ def _inputs():
     return deps
 
 
+def _stamp() -> str:
+    return os.environ.get("JDEC_EXTRA_NVCC_FLAGS", "")
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB):
+    stamp_file = LIB + ".flags"
+    same_flags = os.path.exists(stamp_file) and open(stamp_file).read() == _stamp()
+    if not force and same_flags and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in _inputs()):
             return LIB
@@ -48,6 +54,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
              "-diag-suppress", "1160", "-I", os.path.join(ROOT, "include")] + ARCH
     if verbose:
         flags += ["-Xptxas", "-v"]
+    # developer knob: extra nvcc flags (e.g. -DJDEC_MIN_CTAS=5), part of the staleness key
+    extra = os.environ.get("JDEC_EXTRA_NVCC_FLAGS", "").split()
+    flags += extra
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
@@ -71,6 +80,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(stamp_file, "w") as f:
+        f.write(_stamp())
     return LIB
 
 

@@ -113,9 +113,8 @@ jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers)
     return JDEC_OK;
 }
 
-// Default strip width: as many coefficient blocks per MCU row as IDCT threads
-// (96 for 4:4:4, 64 otherwise), so every IDCT thread transforms one block
-// per job.
+// Default strip width (measured on 8192x8192 images with 64 IDCT threads): about
+// one or two coefficient blocks per IDCT thread per job.
 int default_wt(const Geometry &g)
 {
     if (g.hm == 1) return 32;                 // 3 blocks per MCU
@@ -123,10 +122,9 @@ int default_wt(const Geometry &g)
     return 10;                                // 6 blocks per MCU (+ 4 halo blocks)
 }
 
-// Strip width (MCUs) and chunk height (MCU rows) for `nrows` MCU rows of an
-// image: enough work items to fill every SM at the kernel's occupancy.
-void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int *wt, int *rpc, int *nchunks,
-                int *smem)
+// Strip width (MCUs) and the number of CTAs for `nrows` MCU rows of an image:
+// one full wave (occupancy x SMs) or fewer when there are fewer strip-rows.
+void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int *wt, int *nctas, int *smem)
 {
     int w = force_wt > 0 ? force_wt : tuned_wt(ctx, g);
     if (w <= 0) w = default_wt(g);
@@ -134,19 +132,16 @@ void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int *
     const SmemLayout L = smem_layout(g.hm, g.vm, g.fancy, w, default_slots(g.hm, g.vm, g.fancy));
     const int occ = occupancy_cached(ctx, g.hm, g.vm, g.fancy, L.total);
     const int nstrips = (g.mcus_x + w - 1) / w;
-    const long target = static_cast<long>(occ) * ctx->sms;
-    int nch = static_cast<int>(std::max<long>(1, (target + nstrips - 1) / nstrips));
-    nch = std::min(nch, nrows);
-    int r = (nrows + nch - 1) / nch;
-    const int min_rows = (g.fancy && g.vm == 2) ? 4 : 1;   // amortise the chroma prologue
-    r = std::max(r, std::min(min_rows, nrows));
+    const long rows = static_cast<long>(nstrips) * nrows;
+    // items shorter than a few rows pay the 4:2:0 chroma prologue too often
+    const long min_rows = (g.fancy && g.vm == 2) ? 6 : 1;
+    const long cap = std::max(1L, rows / std::min<long>(min_rows, nrows));
     *wt = w;
-    *rpc = r;
-    *nchunks = (nrows + r - 1) / r;
+    *nctas = static_cast<int>(std::min<long>(static_cast<long>(occ) * ctx->sms, cap));
     *smem = L.total;
 }
 
-void fill_desc(ImageDesc *d, const jdec_image *img, const Geometry &g, int wt, int rpc, int nchunks)
+void fill_desc(ImageDesc *d, const jdec_image *img, const Geometry &g, int wt, int nctas)
 {
     memset(d, 0, sizeof(*d));
     d->rgb = img->rgb;
@@ -156,14 +151,18 @@ void fill_desc(ImageDesc *d, const jdec_image *img, const Geometry &g, int wt, i
     d->cw = g.cw; d->ch = g.ch;
     d->wt = wt;
     d->nstrips = (g.mcus_x + wt - 1) / wt;
-    d->rows_per_chunk = rpc;
-    d->nchunks = nchunks;
+    d->nctas = nctas;
     d->row0 = 0;
     d->row1 = g.mcus_y;
     d->nslot = default_slots(g.hm, g.vm, g.fancy);
+    d->nidct = 32 * default_idct_warps(g.hm, g.vm);
     d->aligned8 = ((reinterpret_cast<uintptr_t>(img->rgb) | static_cast<uintptr_t>(img->rgb_pitch)) & 7) == 0;
+    d->q8 = 1;
     for (int c = 0; c < 3; ++c)
-        for (int k = 0; k < 64; ++k) d->q[c][k] = img->qtab[c][k];
+        for (int k = 0; k < 64; ++k) {
+            d->q[c][k] = img->qtab[c][k];
+            if (img->qtab[c][k] > 255) d->q8 = 0;
+        }
 }
 
 bool encode_maps(CUtensorMap maps[3], const jdec_image *img, const Geometry &g, int wt)
@@ -180,16 +179,18 @@ jdec_status launch_rows(jdec_ctx *ctx, const jdec_image *img, const Geometry &g,
                         int row1, int force_wt)
 {
     if (row1 <= row0) return JDEC_OK;
-    int wt, rpc, nchunks, smem;
-    plan_tiles(ctx, g, row1 - row0, force_wt, &wt, &rpc, &nchunks, &smem);
+    int wt, nctas, smem;
+    plan_tiles(ctx, g, row1 - row0, force_wt, &wt, &nctas, &smem);
     DecodeParams p;
     memset(&p, 0, sizeof(p));
     if (!encode_maps(p.tmap, img, g, wt)) return JDEC_ECUDA;
-    fill_desc(&p.img, img, g, wt, rpc, nchunks);
+    fill_desc(&p.img, img, g, wt, nctas);
+    const int ni = tuned_nidct(ctx, g);
+    if (ni > 0) p.img.nidct = ni;
     p.img.row0 = row0;
     p.img.row1 = row1;
     p.err = ctx->d_err;
-    const int grid = p.img.nstrips * nchunks;
+    const int grid = nctas;
     cudaError_t e = launch_fused(g.hm, g.vm, g.fancy, p, grid, smem, s);
     if (e != cudaSuccess) return JDEC_ECUDA;
     ctx->launches++;

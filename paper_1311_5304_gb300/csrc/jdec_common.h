@@ -7,8 +7,10 @@
 
 namespace jdec {
 
-// Launch shape of the fused kernel: each CTA owns a strip of `wt` MCUs and
-// walks down `rows_per_chunk` MCU rows of it.
+// Launch shape of the fused kernel: the image is cut into strips of `wt` MCUs;
+// the strips' MCU rows, concatenated strip after strip, are split into equal
+// contiguous ranges, one per CTA (a range may end one strip and start the
+// next).
 constexpr int kMaxWT = 32;          // widest strip the shared-memory layout allows
 constexpr int kStages = 2;          // coefficient double buffer
 
@@ -25,11 +27,12 @@ struct ImageDesc {
     int32_t cw, ch;         // true chroma size
     int32_t wt;             // MCUs per strip
     int32_t nstrips;
-    int32_t rows_per_chunk; // MCU rows per CTA work item
-    int32_t nchunks;
+    int32_t nctas;          // CTAs sharing the strip-rows of this image
     int32_t aligned8;       // rgb and pitch are 8-byte aligned
+    int32_t q8;             // every quantisation step fits in 8 bits (dp2a path)
     int32_t row0, row1;     // MCU rows [row0, row1) covered by the launch
     int32_t nslot;          // chroma slots of the shared-memory ring (2 or 4)
+    int32_t nidct;          // threads of the IDCT warp group (32, 64 or 96)
     int32_t q[3][64];       // dequantisation tables, natural order
 };
 
@@ -43,16 +46,18 @@ struct DecodeParams {
 // Threads of a CTA: IDCT warps (producers) + upsample/colour warps (consumers).
 constexpr int kWarps = 4;
 constexpr int kCtaThreads = 32 * kWarps;
-__host__ __device__ inline int idct_warps(int hm) { return hm == 1 ? 3 : 2; }
+__host__ __device__ inline int default_idct_warps(int hm, int vm) { return (void)hm, (void)vm, 2; }
 
 // Shared-memory carve-up of one CTA; identical on host and device.
 //   stages : kStages coefficient tiles written by TMA (1024-aligned regions)
 //   y      : 2 luma sample planes (double buffer), (8*VM) x (8*HM*wt) bytes
 //   c      : nslot chroma slots (4 for 4:2:0 triangular filtering, else 2),
-//            each 2 components x 8 rows x lc bytes
+//            each 2 components x 8 rows x lc bytes (halo blocks included)
+//   q      : dequantisation tables, 3 components x 64 int32 (transposed) or
+//            3 x 32 packed-byte words for the dp2a path
 struct SmemLayout {
     int ny, nc;             // Y blocks per step, chroma blocks per component per step
-    int lc;                 // chroma samples per slot row (with halo blocks)
+    int lc;                 // bytes per chroma slot row
     int stage_y, stage_c;   // byte offsets of the regions inside a stage
     int cbytes;             // bytes of one chroma component region of a stage
     int stage_bytes;        // one coefficient stage
@@ -62,7 +67,7 @@ struct SmemLayout {
     int nslot;              // chroma slots
     int slot_bytes;         // one chroma slot (both components)
     int off_c;              // chroma slots
-    int off_q;              // dequantisation tables, int32 [3][64]
+    int off_q;              // dequantisation tables
     int off_bar;            // mbarriers, one per stage
     int off_flag;           // CTA-wide flags
     int total;              // bytes, including 1024 of alignment slack

@@ -158,36 +158,25 @@ __device__ __forceinline__ void idct8(const int x0, const int x1, const int x2, 
 __device__ __forceinline__ int sext_lo(uint32_t w) { return static_cast<int>(static_cast<int16_t>(w & 0xffffu)); }
 __device__ __forceinline__ int sext_hi(uint32_t w) { return static_cast<int>(w) >> 16; }
 
-// Dequantise + 2-D IDCT one block that TMA placed at shared address `blk`
-// with the 128-byte swizzle (16-byte chunk c of the 128-byte row at address
-// A lives at chunk c ^ ((A >> 7) & 7)).  q: dequantisation table (int32,
-// natural order, shared memory).  Writes the 8x8 samples to `dst` (shared
-// memory, row pitch `pitch` bytes, 8-byte aligned rows).
-__device__ __forceinline__ void idct_block(uint32_t blk, const int *__restrict__ q, uint8_t *dst, int pitch)
+// Two-way dot product of packed signed 16-bit lanes of `a` with unsigned
+// bytes of `b` (low: bytes 0,1; high: bytes 2,3), accumulated into c.
+__device__ __forceinline__ int dp2a_lo(uint32_t a, uint32_t b, int c)
 {
-    const uint32_t sw = (blk >> 7) & 7u;
-    uint32_t w[8][4];
-#pragma unroll
-    for (int v = 0; v < 8; ++v) {
-        const uint4 r = lds128(blk + ((static_cast<uint32_t>(v) ^ sw) << 4));
-        w[v][0] = r.x; w[v][1] = r.y; w[v][2] = r.z; w[v][3] = r.w;
-    }
-    // Eq. 1: column pass over the vertical frequency v for each u.
-    int ws[8][8];   // [y][u], 2 fractional bits
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        int x[8];
-#pragma unroll
-        for (int v = 0; v < 8; ++v) {
-            const uint32_t word = w[v][u >> 1];
-            x[v] = ((u & 1) ? sext_hi(word) : sext_lo(word)) * q[v * 8 + u];
-        }
-        int y[8];
-        idct8(x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7], 1 << 10, y);
-#pragma unroll
-        for (int yy = 0; yy < 8; ++yy) ws[yy][u] = y[yy] >> 11;
-    }
-    // Eq. 2: row pass over u for each spatial row, level shift, clamp.
+    int d;
+    asm("dp2a.lo.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ int dp2a_hi(uint32_t a, uint32_t b, int c)
+{
+    int d;
+    asm("dp2a.hi.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// Row pass (Eq. 2) from the column-pass workspace, level shift and
+// range-limit clamp; 8 samples per row to dst.
+__device__ __forceinline__ void idct_rows(const int ws[8][8], uint8_t *dst, int pitch)
+{
 #pragma unroll
     for (int yy = 0; yy < 8; ++yy) {
         int y[8];
@@ -200,6 +189,79 @@ __device__ __forceinline__ void idct_block(uint32_t blk, const int *__restrict__
     }
 }
 
+// Dequantise + 2-D IDCT one block that TMA placed at shared address `blk`
+// with the 128-byte swizzle (16-byte chunk c of the 128-byte row at address
+// A lives at chunk c ^ ((A >> 7) & 7)).  qt: dequantisation table (int32,
+// shared memory, 16-byte aligned) stored transposed, qt[8*u + v] = Q(u, v),
+// so each column's eight steps are two 16-byte loads.  Writes the 8x8
+// samples to `dst` (shared memory, row pitch `pitch` bytes, 8-byte aligned
+// rows).
+__device__ __forceinline__ void idct_block(uint32_t blk, const int *__restrict__ qt, uint8_t *dst, int pitch)
+{
+    const uint32_t sw = (blk >> 7) & 7u;
+    uint32_t w[8][4];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const uint4 r = lds128(blk + ((static_cast<uint32_t>(v) ^ sw) << 4));
+        w[v][0] = r.x; w[v][1] = r.y; w[v][2] = r.z; w[v][3] = r.w;
+    }
+    // Eq. 1: column pass over the vertical frequency v for each u.
+    int ws[8][8];   // [y][u], 2 fractional bits
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int4 qa = *reinterpret_cast<const int4 *>(qt + 8 * u);
+        const int4 qb = *reinterpret_cast<const int4 *>(qt + 8 * u + 4);
+        const int qv[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+        int x[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const uint32_t word = w[v][u >> 1];
+            x[v] = ((u & 1) ? sext_hi(word) : sext_lo(word)) * qv[v];
+        }
+        int y[8];
+        idct8(x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7], 1 << 10, y);
+#pragma unroll
+        for (int yy = 0; yy < 8; ++yy) ws[yy][u] = y[yy] >> 11;
+    }
+    // Eq. 2: row pass over u for each spatial row, level shift, clamp.
+    idct_rows(ws, dst, pitch);
+}
+
+// Same transform for quantisation steps that fit in 8 bits: sign extension
+// and dequantisation of a coefficient pair take one dp2a each.  qw: 32 words,
+// qw[8*p + v] = Q(2p, v) | Q(2p+1, v) << 24 (column pair p, row v).
+__device__ __forceinline__ void idct_block_q8(uint32_t blk, const uint32_t *__restrict__ qw, uint8_t *dst, int pitch)
+{
+    const uint32_t sw = (blk >> 7) & 7u;
+    uint32_t w[8][4];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const uint4 r = lds128(blk + ((static_cast<uint32_t>(v) ^ sw) << 4));
+        w[v][0] = r.x; w[v][1] = r.y; w[v][2] = r.z; w[v][3] = r.w;
+    }
+    int ws[8][8];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const uint4 qa = *reinterpret_cast<const uint4 *>(qw + 8 * p);
+        const uint4 qb = *reinterpret_cast<const uint4 *>(qw + 8 * p + 4);
+        const uint32_t qv[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+        int xl[8], xh[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            xl[v] = dp2a_lo(w[v][p], qv[v], 0);
+            xh[v] = dp2a_hi(w[v][p], qv[v], 0);
+        }
+        int y[8];
+        idct8(xl[0], xl[1], xl[2], xl[3], xl[4], xl[5], xl[6], xl[7], 1 << 10, y);
+#pragma unroll
+        for (int yy = 0; yy < 8; ++yy) ws[yy][2 * p] = y[yy] >> 11;
+        idct8(xh[0], xh[1], xh[2], xh[3], xh[4], xh[5], xh[6], xh[7], 1 << 10, y);
+#pragma unroll
+        for (int yy = 0; yy < 8; ++yy) ws[yy][2 * p + 1] = y[yy] >> 11;
+    }
+    idct_rows(ws, dst, pitch);
+}
+
 // ---------------------------------------------------------------------------
 // Colour conversion (Sec. 4.3, Alg. 2) in 16-bit fixed point with the
 // chroma offset and the rounding folded into one constant per channel:
@@ -207,25 +269,30 @@ __device__ __forceinline__ void idct_block(uint32_t blk, const int *__restrict__
 //   G = Y + ((-22554 Cb - 46802 Cr + 8910336) >> 16)
 //   B = Y + ((116130 Cb - 14831872) >> 16)
 // (91881 = round(1.402 * 2^16), 22554, 46802, 116130 likewise; the constant
-// terms are -c*128*2^16/2^16 + 2^15.)  Y is added before the shift as
-// Y * 2^16, which is exact.  Saturation happens in the byte pack.
+// terms are -c*128*2^16/2^16 + 2^15.)  Y enters as Y * 2^16 before the shift,
+// which is exact.  Saturation happens in the byte pack.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void ycc_rgb(int y, int cb, int cr, int &r, int &g, int &b)
+
+// Byte k of w as an int / placed at bits 16..23 (PRMT with zero fill).
+__device__ __forceinline__ int byte_of(uint32_t w, int k) { return static_cast<int>(__byte_perm(w, 0u, 0x4440u | k)); }
+__device__ __forceinline__ int byte_hi16(uint32_t w, int k)
 {
-    const int ys = y << 16;
-    r = (ys + cr * 91881 - 11728000) >> 16;
-    g = (ys - cb * 22554 - cr * 46802 + 8910336) >> 16;
-    b = (ys + cb * 116130 - 14831872) >> 16;
+    return static_cast<int>(__byte_perm(w, 0u, 0x4044u | (static_cast<uint32_t>(k) << 8)));
 }
 
-// Converts 8 pixels and writes 24 bytes to `out` (global).  `n` = pixels
-// inside the image (1..8); `vec` = the 8-byte vector path is allowed.
-__device__ __forceinline__ void cc_store8(const int Y[8], const int Cb[8], const int Cr[8],
-                                          uint8_t *out, int n, bool vec)
+// Converts 8 pixels and writes 24 bytes to `out` (global).  yw: the 8 luma
+// samples as two words; `n` = pixels inside the image (1..8); `vec` = the
+// 8-byte vector path is allowed.
+__device__ __forceinline__ void cc_store8(uint2 yw, const int Cb[8], const int Cr[8], uint8_t *out, int n, bool vec)
 {
     int R[8], G[8], B[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) ycc_rgb(Y[k], Cb[k], Cr[k], R[k], G[k], B[k]);
+    for (int k = 0; k < 8; ++k) {
+        const int ys = byte_hi16(k < 4 ? yw.x : yw.y, k & 3);
+        R[k] = (ys + Cr[k] * 91881 - 11728000) >> 16;
+        G[k] = (ys - Cb[k] * 22554 - Cr[k] * 46802 + 8910336) >> 16;
+        B[k] = (ys + Cb[k] * 116130 - 14831872) >> 16;
+    }
     if (vec && n == 8) {
         uint2 *o = reinterpret_cast<uint2 *>(out);
         o[0] = make_uint2(pack_sat4(R[0], G[0], B[0], R[1]), pack_sat4(G[1], B[1], R[2], G[2]));
@@ -241,17 +308,6 @@ __device__ __forceinline__ void cc_store8(const int Y[8], const int Cb[8], const
             }
         }
     }
-}
-
-__device__ __forceinline__ int byte_of(uint32_t w, int i) { return (w >> (8 * i)) & 0xff; }
-
-// Eight consecutive samples of a shared plane row starting at an 8-byte
-// aligned address.
-__device__ __forceinline__ void load8(const uint8_t *p, int v[8])
-{
-    const uint2 w = *reinterpret_cast<const uint2 *>(p);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) { v[k] = byte_of(w.x, k); v[4 + k] = byte_of(w.y, k); }
 }
 
 // Six samples p[-1 .. 4] around four chroma centres starting at the 4-byte
@@ -271,8 +327,9 @@ __device__ __forceinline__ void tri_h2v1(const int c[6], int o[8])
 {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        o[2 * k] = (3 * c[k + 1] + c[k] + 1) >> 2;
-        o[2 * k + 1] = (3 * c[k + 1] + c[k + 2] + 2) >> 2;
+        const int t = 3 * c[k + 1];
+        o[2 * k] = (t + c[k] + 1) >> 2;
+        o[2 * k + 1] = (t + c[k + 2] + 2) >> 2;
     }
 }
 
@@ -285,8 +342,9 @@ __device__ __forceinline__ void tri_h2v2(const int n[6], const int f[6], int o[8
     for (int k = 0; k < 6; ++k) s[k] = 3 * n[k] + f[k];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        o[2 * k] = (3 * s[k + 1] + s[k] + 8) >> 4;
-        o[2 * k + 1] = (3 * s[k + 1] + s[k + 2] + 7) >> 4;
+        const int t = 3 * s[k + 1];
+        o[2 * k] = (t + s[k] + 8) >> 4;
+        o[2 * k + 1] = (t + s[k + 2] + 7) >> 4;
     }
 }
 

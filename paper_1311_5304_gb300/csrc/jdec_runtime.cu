@@ -30,12 +30,24 @@ int size_class_of(const Geometry &g)
     return c / 2;   // buckets of 4x in MCU count
 }
 
-int tuned_wt(jdec_ctx *ctx, const Geometry &g)
+static const TuneEntry *tuned(jdec_ctx *ctx, const Geometry &g)
 {
     const int v = variant_of(g), sc = size_class_of(g);
     for (int i = 0; i < ctx->n_tune; ++i)
-        if (ctx->tune[i].variant == v && ctx->tune[i].size_class == sc) return ctx->tune[i].wt;
-    return 0;
+        if (ctx->tune[i].variant == v && ctx->tune[i].size_class == sc) return &ctx->tune[i];
+    return nullptr;
+}
+
+int tuned_wt(jdec_ctx *ctx, const Geometry &g)
+{
+    const TuneEntry *t = tuned(ctx, g);
+    return t ? t->wt : 0;
+}
+
+int tuned_nidct(jdec_ctx *ctx, const Geometry &g)
+{
+    const TuneEntry *t = tuned(ctx, g);
+    return t ? t->nidct : 0;
 }
 
 static const char *tune_path(jdec_ctx *ctx)
@@ -45,7 +57,8 @@ static const char *tune_path(jdec_ctx *ctx)
     return (e && e[0]) ? e : nullptr;
 }
 
-// Table format: {"gpu": "<name>", "sms": N, "entries": [[variant, size_class, wt], ...]}
+// Table format: {"gpu": "<name>", "sms": N, "entries": [[variant, size_class, wt, idct_threads], ...]}
+// (idct_threads may be omitted or 0: default split)
 void load_tune_table(jdec_ctx *ctx)
 {
     const char *path = tune_path(ctx);
@@ -68,9 +81,11 @@ void load_tune_table(jdec_ctx *ctx)
     while (ctx->n_tune < 64) {
         const char *q = strchr(p, '[');
         if (!q) break;
-        int v, sc, wt;
-        if (sscanf(q, "[%d , %d , %d]", &v, &sc, &wt) != 3 && sscanf(q, "[%d,%d,%d]", &v, &sc, &wt) != 3) break;
-        if (wt >= 1 && wt <= kMaxWT) ctx->tune[ctx->n_tune++] = TuneEntry{v, sc, wt};
+        int v = 0, sc = 0, wt = 0, ni = 0;
+        const int got = sscanf(q, "[ %d , %d , %d , %d", &v, &sc, &wt, &ni);
+        if (got < 3) break;
+        if (got < 4 || (ni != 32 && ni != 64 && ni != 96)) ni = 0;
+        if (wt >= 1 && wt <= kMaxWT) ctx->tune[ctx->n_tune++] = TuneEntry{v, sc, wt, ni};
         p = strchr(q, ']');
         if (!p) break;
         ++p;
@@ -87,7 +102,8 @@ void save_tune_table(jdec_ctx *ctx)
     if (!f) return;
     fprintf(f, "{\"gpu\": \"%s\", \"sms\": %d, \"entries\": [", prop.name, ctx->sms);
     for (int i = 0; i < ctx->n_tune; ++i)
-        fprintf(f, "%s[%d, %d, %d]", i ? ", " : "", ctx->tune[i].variant, ctx->tune[i].size_class, ctx->tune[i].wt);
+        fprintf(f, "%s[%d, %d, %d, %d]", i ? ", " : "", ctx->tune[i].variant, ctx->tune[i].size_class, ctx->tune[i].wt,
+                ctx->tune[i].nidct);
     fprintf(f, "]}\n");
     fclose(f);
 }
@@ -122,7 +138,7 @@ void autotune_shape(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cud
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best > 0) {
-        ctx->tune[ctx->n_tune++] = TuneEntry{variant_of(g), size_class_of(g), best};
+        ctx->tune[ctx->n_tune++] = TuneEntry{variant_of(g), size_class_of(g), best, 0};
         save_tune_table(ctx);
     }
 }

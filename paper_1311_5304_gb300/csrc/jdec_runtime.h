@@ -26,6 +26,7 @@ struct TuneEntry {
     int variant;     // 0: 4:4:4, 1: 4:2:2 replicate, 2: 4:2:2 fancy, 3: 4:2:0 replicate, 4: 4:2:0 fancy
     int size_class;  // log2 of the MCU count, bucketed
     int wt;
+    int nidct;       // IDCT threads (0: default split)
 };
 
 struct BatchState;
@@ -62,9 +63,8 @@ namespace jdec {
 const char *status_str(jdec_status s);
 bool encode_plane_map(CUtensorMap *m, const int16_t *base, int bw, int bh, int box_w, int box_h);
 jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers);
-void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int *wt, int *rpc, int *nchunks,
-                int *smem);
-void fill_desc(ImageDesc *d, const jdec_image *img, const Geometry &g, int wt, int rpc, int nchunks);
+void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int *wt, int *nctas, int *smem);
+void fill_desc(ImageDesc *d, const jdec_image *img, const Geometry &g, int wt, int nctas);
 bool encode_maps(CUtensorMap maps[3], const jdec_image *img, const Geometry &g, int wt);
 jdec_status launch_rows(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cudaStream_t s, int row0,
                         int row1, int force_wt);
@@ -76,6 +76,7 @@ int variant_of(const Geometry &g);
 int default_wt(const Geometry &g);
 int size_class_of(const Geometry &g);
 int tuned_wt(jdec_ctx *ctx, const Geometry &g);
+int tuned_nidct(jdec_ctx *ctx, const Geometry &g);
 void load_tune_table(jdec_ctx *ctx);
 void save_tune_table(jdec_ctx *ctx);
 void autotune_shape(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cudaStream_t s);

@@ -9,9 +9,9 @@
 //                block per thread into shared sample planes, refill the TMA
 //                stage with the tile two jobs ahead, replicate the true chroma
 //                edge into halo columns at image edges, signal FULL[job % 2];
-//   colour warps wait FULL[job % 2], upsample chroma and convert 8 pixels (or
-//                8 pixels x 2 rows for 4:2:0) per task to RGB with 8-byte
-//                vector stores, signal EMPTY[job % 2].
+//   colour warps wait FULL[job % 2], upsample chroma and convert 8 pixels of
+//                one output row per task to RGB with 8-byte vector stores,
+//                signal EMPTY[job % 2].
 // The IDCT warps wait EMPTY[job % 2] before overwriting the planes of job-2.
 // Luma planes are double-buffered; chroma rows go to a ring of four slots in
 // job order, so a 4:2:0 triangular filter finds chroma rows r-1, r, r+1 in
@@ -36,8 +36,6 @@ struct Variant {
     static constexpr bool kRing = FANCY && HM == 2 && VM == 2; // vertical neighbours
     static constexpr int kLA = kRing ? 1 : 0;                  // chroma lookahead rows
     static constexpr int kPro = kRing ? 2 : 0;                 // chroma-only jobs per item
-    static constexpr int kIdctThreads = 32 * (HM == 1 ? 3 : 2);
-    static constexpr int kCcThreads = kCtaThreads - kIdctThreads;
 };
 
 // Job k of an item covering MCU rows [r0, r1): its luma row (-1: none) and
@@ -73,84 +71,67 @@ __device__ __forceinline__ void issue_job(const CUtensorMap *tm, const SmemLayou
 }
 
 // ---------------------------------------------------------------------------
-// colour warps: one task
+// colour warps: one task = 8 pixels of one output row
 // ---------------------------------------------------------------------------
 template <int HM, int VM, bool FANCY>
 __device__ __forceinline__ void cc_task(const ImageDesc &d, const SmemLayout &L, const uint8_t *yplane,
-                                        const uint8_t *cslots, int job, int r, int mx0, int t, int ngroups)
+                                        const uint8_t *cslots, int job, int r, int mx0, int py, int g)
 {
-    const int lc = L.lc;
-    const int pr = t / ngroups, g = t - pr * ngroups;
     const int x0 = (mx0 * HM + g) * 8;
-    if (x0 >= d.W) return;
+    const int y = r * 8 * VM + py;
+    if (x0 >= d.W || y >= d.H) return;
     const int n = min(8, d.W - x0);
     const bool vec = d.aligned8 != 0;
-    const uint8_t *cb_cur = cslots + (job & (L.nslot - 1)) * L.slot_bytes;
-    if (VM == 1) {
-        const int y = r * 8 + pr;
-        if (y >= d.H) return;
-        int Yv[8], Cb[8], Cr[8];
-        load8(yplane + pr * L.ypitch + 8 * g, Yv);
-        const uint8_t *cb = cb_cur + pr * lc;
-        const uint8_t *cr = cb + 8 * lc;
-        if (HM == 1) {
-            load8(cb + 8 * g, Cb);
-            load8(cr + 8 * g, Cr);
-        } else if (!FANCY) {
-            const uint32_t wb = *reinterpret_cast<const uint32_t *>(cb + 4 * g);
-            const uint32_t wr = *reinterpret_cast<const uint32_t *>(cr + 4 * g);
+    const uint2 yw = *reinterpret_cast<const uint2 *>(yplane + py * L.ypitch + 8 * g);
+    int Cb[8], Cr[8];
+    if (HM == 1) {
+        // 4:4:4: chroma sample = pixel
+        const uint8_t *cb = cslots + (job & (L.nslot - 1)) * L.slot_bytes + py * L.lc + 8 * g;
+        const uint2 wb = *reinterpret_cast<const uint2 *>(cb);
+        const uint2 wr = *reinterpret_cast<const uint2 *>(cb + 8 * L.lc);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) { Cb[k] = byte_of(wb, k >> 1); Cr[k] = byte_of(wr, k >> 1); }
-        } else {
-            int cb6[6], cr6[6];
-            load6(cb + 8 + 4 * g, cb6);
-            load6(cr + 8 + 4 * g, cr6);
-            tri_h2v1(cb6, Cb);
-            tri_h2v1(cr6, Cr);
+        for (int k = 0; k < 4; ++k) {
+            Cb[k] = byte_of(wb.x, k); Cb[4 + k] = byte_of(wb.y, k);
+            Cr[k] = byte_of(wr.x, k); Cr[4 + k] = byte_of(wr.y, k);
         }
-        cc_store8(Yv, Cb, Cr, d.rgb + static_cast<int64_t>(y) * d.pitch + 3 * x0, n, vec);
+    } else if (!FANCY) {
+        // replication: chroma sample (x/2, y/VM)
+        const uint8_t *cb = cslots + (job & (L.nslot - 1)) * L.slot_bytes + (VM == 2 ? (py >> 1) : py) * L.lc + 4 * g;
+        const uint32_t wb = *reinterpret_cast<const uint32_t *>(cb);
+        const uint32_t wr = *reinterpret_cast<const uint32_t *>(cb + 8 * L.lc);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            Cb[2 * k] = Cb[2 * k + 1] = byte_of(wb, k);
+            Cr[2 * k] = Cr[2 * k + 1] = byte_of(wr, k);
+        }
+    } else if (VM == 1) {
+        // h2v1 triangular (Alg. 1); the slot row starts one halo block left
+        const uint8_t *cb = cslots + (job & (L.nslot - 1)) * L.slot_bytes + py * L.lc + 8 + 4 * g;
+        int c6[6];
+        load6(cb, c6);
+        tri_h2v1(c6, Cb);
+        load6(cb + 8 * L.lc, c6);
+        tri_h2v1(c6, Cr);
     } else {
-        // output rows 2*pr and 2*pr + 1 of the MCU row share chroma row j
-        const int y = r * 16 + 2 * pr;
-        if (y >= d.H) return;
-        const bool two = y + 1 < d.H;
-        int Y0[8], Y1[8], Cb0[8], Cr0[8], Cb1[8], Cr1[8];
-        load8(yplane + (2 * pr) * L.ypitch + 8 * g, Y0);
-        load8(yplane + (2 * pr + 1) * L.ypitch + 8 * g, Y1);
-        if (!FANCY) {
-            const uint8_t *cb = cb_cur + pr * lc;
-            const uint32_t wb = *reinterpret_cast<const uint32_t *>(cb + 4 * g);
-            const uint32_t wr = *reinterpret_cast<const uint32_t *>(cb + 8 * lc + 4 * g);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                Cb0[k] = Cb1[k] = byte_of(wb, k >> 1);
-                Cr0[k] = Cr1[k] = byte_of(wr, k >> 1);
-            }
-        } else {
-            // chroma block row b lives in slot (job - 1 + b - r) & 3
-            const int j = y >> 1;
-            const int ju = max(j - 1, 0), jd = min(j + 1, d.ch - 1);
-            auto row_ptr = [&](int jr) {
-                return cslots + ((job - 1 + (jr >> 3) - r) & 3) * L.slot_bytes + (jr & 7) * lc + 8 + 4 * g;
-            };
-            const uint8_t *pn = row_ptr(j), *pu = row_ptr(ju), *pd = row_ptr(jd);
-            int n6[6], u6[6], d6[6];
-            load6(pn, n6); load6(pu, u6); load6(pd, d6);
-            tri_h2v2(n6, u6, Cb0);
-            tri_h2v2(n6, d6, Cb1);
-            load6(pn + 8 * lc, n6); load6(pu + 8 * lc, u6); load6(pd + 8 * lc, d6);
-            tri_h2v2(n6, u6, Cr0);
-            tri_h2v2(n6, d6, Cr1);
-        }
-        uint8_t *out = d.rgb + static_cast<int64_t>(y) * d.pitch + 3 * x0;
-        cc_store8(Y0, Cb0, Cr0, out, n, vec);
-        if (two) cc_store8(Y1, Cb1, Cr1, out + d.pitch, n, vec);
+        // h2v2 triangular: chroma row j = y/2 (near) and j-1 / j+1 (far, for
+        // even / odd output rows, clamped); chroma block row b lives in slot
+        // (job - 1 + b - r) & 3
+        const int j = y >> 1;
+        const int jf = min(max(j + ((py & 1) ? 1 : -1), 0), d.ch - 1);
+        const uint8_t *pn = cslots + ((job - 1 + (j >> 3) - r) & 3) * L.slot_bytes + (j & 7) * L.lc + 8 + 4 * g;
+        const uint8_t *pf = cslots + ((job - 1 + (jf >> 3) - r) & 3) * L.slot_bytes + (jf & 7) * L.lc + 8 + 4 * g;
+        int n6[6], f6[6];
+        load6(pn, n6); load6(pf, f6);
+        tri_h2v2(n6, f6, Cb);
+        load6(pn + 8 * L.lc, n6); load6(pf + 8 * L.lc, f6);
+        tri_h2v2(n6, f6, Cr);
     }
+    cc_store8(yw, Cb, Cr, d.rgb + static_cast<int64_t>(y) * d.pitch + 3 * x0, n, vec);
 }
 
 // Replicates the true chroma edge into halo/padding columns of the 8 rows of
 // both components of one chroma slot (strips at the image's left or right
-// edge only).  `tid` < 16 does one row each.
+// edge only, triangular filtering only).  Thread `tid` < 16 does one row.
 __device__ __forceinline__ void fix_edges(uint8_t *slot, int lc, int mx0, int cw, int used, int tid)
 {
     if (tid >= 16) return;
@@ -167,11 +148,11 @@ __device__ __forceinline__ void fix_edges(uint8_t *slot, int lc, int mx0, int cw
     }
 }
 
-// Runs one work item with the whole CTA.  `smem` is 1024-byte aligned.
+// Runs one work item (MCU rows [r0, r1) of one strip) with the whole CTA.  `smem` is 1024-byte aligned.
 // Returns false if a bounded wait gave up (the error word has been set; the
 // CTA must stop).  `last` = this is the CTA's final item (drain barriers).
-template <int HM, int VM, bool FANCY>
-__device__ bool run_work(const CUtensorMap *tm, const ImageDesc &d, int strip, int chunk, uint8_t *smem,
+template <int HM, int VM, bool FANCY, bool Q8>
+__device__ bool run_work(const CUtensorMap *tm, const ImageDesc &d, int strip, int r0, int r1, uint8_t *smem,
                          PipeState &ps, int *err, bool last)
 {
     using V = Variant<HM, VM, FANCY>;
@@ -180,8 +161,6 @@ __device__ bool run_work(const CUtensorMap *tm, const ImageDesc &d, int strip, i
     const int wt = d.wt;
     const int mx0 = strip * wt;
     const int wte = min(wt, d.mcus_x - mx0);
-    const int r0 = d.row0 + chunk * d.rows_per_chunk;
-    const int r1 = min(r0 + d.rows_per_chunk, d.row1);
     if (r0 >= r1 || wte <= 0) return true;
     const int njobs = V::kPro + (r1 - r0);
     const int J0 = ps.job;
@@ -192,15 +171,16 @@ __device__ bool run_work(const CUtensorMap *tm, const ImageDesc &d, int strip, i
     const uint32_t bar0 = smem_u32(smem + L.off_bar);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L.off_flag);
 
-    if (tid < V::kIdctThreads) {
+    const int nidct = d.nidct, ncc = kCtaThreads - d.nidct;
+    if (tid < nidct) {
         // =================== IDCT warps ===================
         const int *qs = reinterpret_cast<const int *>(smem + L.off_q);
         const int lb0 = (V::kHalo && mx0 == 0) ? 1 : 0;
         const int lb1 = min(wte + (V::kHalo ? 2 : 0), d.mcus_x - (mx0 - (V::kHalo ? 1 : 0)));
         const int nce = lb1 - lb0;
+        const int nye = VM * HM * wte;
         const int used = 8 * (wte + (V::kHalo ? 2 : 0));
         const bool edge = V::kHalo && (mx0 == 0 || d.cw + 7 - 8 * mx0 < used - 1);
-        const int nye = VM * HM * wte;
         const uint64_t budget = 2000000000ull;   // 2 s per wait
 
         if (tid == 0) {
@@ -225,7 +205,7 @@ __device__ bool run_work(const CUtensorMap *tm, const ImageDesc &d, int strip, i
             uint8_t *yplane = yplanes + s * L.ybytes;
             uint8_t *slot = cslots + (j & (L.nslot - 1)) * L.slot_bytes;
             const int ntask = (yrow >= 0 ? nye : 0) + (do_c ? 2 * nce : 0);
-            for (int t = tid; ok && t < ntask; t += V::kIdctThreads) {
+            for (int t = tid; ok && t < ntask; t += nidct) {
                 uint32_t blk;
                 const int *q;
                 uint8_t *dst;
@@ -246,9 +226,12 @@ __device__ bool run_work(const CUtensorMap *tm, const ImageDesc &d, int strip, i
                     dst = slot + comp * 8 * L.lc + 8 * lb;
                     pitch = L.lc;
                 }
-                idct_block(blk, q, dst, pitch);
+                if (Q8)
+                    idct_block_q8(blk, reinterpret_cast<const uint32_t *>(q), dst, pitch);
+                else
+                    idct_block(blk, q, dst, pitch);
             }
-            named_sync(kBarIdct, V::kIdctThreads);
+            named_sync(kBarIdct, nidct);
             if (*abort_flag) {
                 if (tid == 0) {
                     atomicExch(err, kErrTimeout);
@@ -276,9 +259,12 @@ __device__ bool run_work(const CUtensorMap *tm, const ImageDesc &d, int strip, i
         }
     } else {
         // =================== colour warps ===================
-        const int tc = tid - V::kIdctThreads;
+        const int tc = tid - nidct;
         const int ngroups = HM * wte;
-        const int ntask = 8 * ngroups;   // 8 rows (or row pairs) x 8-pixel groups
+        const int rows = 8 * VM;
+        // this thread's first task (row, group) and the per-step advance
+        const int py0 = tc / ngroups, g0 = tc - py0 * ngroups;
+        const int dpy = ncc / ngroups, dg = ncc - dpy * ngroups;
         for (int k = 0; k < njobs; ++k) {
             const int j = J0 + k, s = j & 1;
             named_sync(kBarFull0 + s, kCtaThreads);
@@ -286,12 +272,43 @@ __device__ bool run_work(const CUtensorMap *tm, const ImageDesc &d, int strip, i
             if (k >= V::kPro) {
                 const int r = r0 + k - V::kPro;
                 const uint8_t *yplane = yplanes + s * L.ybytes;
-                for (int t = tc; t < ntask; t += V::kCcThreads)
-                    cc_task<HM, VM, FANCY>(d, L, yplane, cslots, j, r, mx0, t, ngroups);
+                int py = py0, g = g0;
+                while (py < rows) {
+                    cc_task<HM, VM, FANCY>(d, L, yplane, cslots, j, r, mx0, py, g);
+                    py += dpy;
+                    g += dg;
+                    if (g >= ngroups) { g -= ngroups; ++py; }
+                }
             }
             named_arrive(kBarEmpty0 + s, kCtaThreads);
         }
         ps.job = J0 + njobs;
+    }
+    return true;
+}
+
+}  // namespace jdec
+
+namespace jdec {
+
+// Runs this CTA's share of an image: the strips' MCU rows in [row0, row1),
+// concatenated strip after strip, split evenly over `nctas` CTAs; `b` is the
+// CTA's index among them.
+template <int HM, int VM, bool FANCY, bool Q8>
+__device__ bool run_share(const CUtensorMap *tm, const ImageDesc &d, int b, uint8_t *smem, PipeState &ps, int *err,
+                          bool last_image)
+{
+    const long nrows = d.row1 - d.row0;
+    const long total = nrows * d.nstrips;
+    long a = total * b / d.nctas;
+    const long e = total * (b + 1) / d.nctas;
+    while (a < e) {
+        const int s = static_cast<int>(a / nrows);
+        const int rr = static_cast<int>(a - s * nrows);
+        const int len = static_cast<int>(min(e - a, nrows - rr));
+        a += len;
+        if (!run_work<HM, VM, FANCY, Q8>(tm, d, s, d.row0 + rr, d.row0 + rr + len, smem, ps, err, last_image && a >= e))
+            return false;
     }
     return true;
 }

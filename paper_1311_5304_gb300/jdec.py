@@ -47,14 +47,17 @@ def library_path() -> str:
     return os.path.join(_HERE, "_build", "libjdec.so")
 
 
-def load(build_if_missing: bool = True):
+def load(build_if_missing: bool = True, path: str | None = None):
     """Loads ``libjdec.so`` (building it first when it is missing or stale and
-    nvcc is available).  Raises if the library cannot be loaded."""
+    nvcc is available), or the library at ``path``.  Raises if the library
+    cannot be loaded."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        path = library_path()
+        if path is not None:
+            build_if_missing = False
+        path = path or library_path()
         if build_if_missing:
             try:
                 from . import build as _b
