@@ -36,6 +36,37 @@ struct ImageDesc {
     int32_t q[3][64];       // dequantisation tables, natural order
 };
 
+// Region offsets shared by every variant decoded by one persistent launch:
+// each variant keeps its own pitches and stage-internal offsets, but stages,
+// planes and slots sit at the same places whatever the variant, so jobs of
+// consecutive items of different variants can overlap in the pipeline.
+struct UnionLayout {
+    int stage_bytes, off_y, ybytes, off_c, slot_bytes, off_q, off_bar, off_flag, total;
+};
+
+// One image of a batched launch (device memory, 128-byte aligned: the tensor
+// maps are read from global memory by TMA).
+struct alignas(128) BatchImage {
+    CUtensorMap tmap[3];
+    ImageDesc desc;
+    int32_t variant;        // 0: 4:4:4, 1: 4:2:2 replicate, 2: 4:2:2 fancy, 3: 4:2:0 replicate, 4: 4:2:0 fancy
+};
+
+// A run of MCU rows [r0, r1) of one strip of one image.
+struct BatchItem {
+    int32_t img, strip, r0, r1;
+};
+
+// Kernel parameters of the batched launch.  CTA b runs items
+// [cta_first[b], cta_first[b+1]) in order.
+struct BatchParams {
+    const BatchImage *imgs;
+    const BatchItem *items;
+    const int32_t *cta_first;
+    UnionLayout U;
+    int *err;
+};
+
 // Kernel parameters of the single-image launch.
 struct DecodeParams {
     CUtensorMap tmap[3];    // coefficient planes, 3-D {64, blocks_w, blocks_h}
@@ -74,6 +105,22 @@ struct SmemLayout {
 };
 
 __host__ __device__ inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline SmemLayout apply_union(SmemLayout L, const UnionLayout &U)
+{
+    L.stage_bytes = U.stage_bytes;
+    L.off_stage = 0;
+    L.off_y = U.off_y;
+    L.ybytes = U.ybytes;
+    L.nslot = 4;
+    L.off_c = U.off_c;
+    L.slot_bytes = U.slot_bytes;
+    L.off_q = U.off_q;
+    L.off_bar = U.off_bar;
+    L.off_flag = U.off_flag;
+    L.total = U.total;
+    return L;
+}
 
 __host__ __device__ inline int default_slots(int hm, int vm, bool fancy) { return (fancy && hm == 2 && vm == 2) ? 4 : 2; }
 

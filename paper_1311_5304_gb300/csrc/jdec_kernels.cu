@@ -28,18 +28,7 @@ __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_fused_kernel(
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = align1024(smem_raw);
     const SmemLayout L = smem_layout(HM, VM, FANCY, p.img.wt, p.img.nslot);
-    int *qs = reinterpret_cast<int *>(smem + L.off_q);
-    if (Q8) {
-        // packed per component: word 8*pr + v = Q_c(v, 2pr) | Q_c(v, 2pr+1) << 24
-        for (int i = threadIdx.x; i < 96; i += blockDim.x) {
-            const int c = i >> 5, pr = (i >> 3) & 3, v = i & 7;
-            qs[64 * c + 8 * pr + v] = p.img.q[c][8 * v + 2 * pr] | (p.img.q[c][8 * v + 2 * pr + 1] << 24);
-        }
-    } else {
-        // transposed per component: qs[64*c + 8*u + v] = Q_c(v, u)
-        for (int i = threadIdx.x; i < 192; i += blockDim.x)
-            qs[i] = p.img.q[i >> 6][((i & 7) << 3) | ((i >> 3) & 7)];
-    }
+    load_qtables<Q8>(reinterpret_cast<int *>(smem + L.off_q), p.img, threadIdx.x, blockDim.x);
     if (threadIdx.x == 0) {
         *reinterpret_cast<volatile int *>(smem + L.off_flag) = 0;
         for (int s = 0; s < kStages; ++s) mbar_init(smem_u32(smem + L.off_bar + 8 * s), 1);
@@ -48,7 +37,85 @@ __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_fused_kernel(
     }
     __syncthreads();
     PipeState ps{0u, 0};
-    run_share<HM, VM, FANCY, Q8>(p.tmap, p.img, blockIdx.x, smem, ps, p.err, true);
+    run_share<HM, VM, FANCY, Q8>(p.tmap, p.img, blockIdx.x, smem, L, ps, p.err, true);
+}
+
+// One item of a batch with its variant's code and the union layout.
+template <int HM, int VM, bool FANCY, bool Q8>
+__device__ __forceinline__ bool batch_item(const BatchParams &p, const BatchImage &bi, const BatchItem &it, uint8_t *smem,
+                                           PipeState &ps, bool last, bool reload)
+{
+    const SmemLayout L = apply_union(smem_layout(HM, VM, FANCY, bi.desc.wt, 4), p.U);
+    if (reload && threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) {
+            tensormap_acquire(&bi.tmap[c]);
+            tma_prefetch_map(&bi.tmap[c]);
+        }
+    return run_work<HM, VM, FANCY, Q8>(bi.tmap, bi.desc, it.strip, it.r0, it.r1, smem, L, ps, p.err, last, reload);
+}
+
+//   jdec_batch_kernel: many images of any variants; CTA b runs the items
+//     [cta_first[b], cta_first[b+1]) of a flattened (image, strip, row range)
+//     work list, pipelined across item boundaries.
+__global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_batch_kernel(const __grid_constant__ BatchParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = align1024(smem_raw);
+    if (threadIdx.x == 0) {
+        *reinterpret_cast<volatile int *>(smem + p.U.off_flag) = 0;
+        for (int s = 0; s < kStages; ++s) mbar_init(smem_u32(smem + p.U.off_bar + 8 * s), 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    PipeState ps{0u, 0};
+    const int i0 = p.cta_first[blockIdx.x], i1 = p.cta_first[blockIdx.x + 1];
+    int cur = -1;
+    for (int i = i0; i < i1; ++i) {
+        const BatchItem it = p.items[i];
+        const BatchImage &bi = p.imgs[it.img];
+        const bool reload = it.img != cur;
+        cur = it.img;
+        const bool last = i + 1 == i1;
+        bool ok;
+        const bool q8 = bi.desc.q8 != 0;
+        switch (bi.variant) {
+        case 0: ok = q8 ? batch_item<1, 1, false, true>(p, bi, it, smem, ps, last, reload)
+                        : batch_item<1, 1, false, false>(p, bi, it, smem, ps, last, reload); break;
+        case 1: ok = q8 ? batch_item<2, 1, false, true>(p, bi, it, smem, ps, last, reload)
+                        : batch_item<2, 1, false, false>(p, bi, it, smem, ps, last, reload); break;
+        case 2: ok = q8 ? batch_item<2, 1, true, true>(p, bi, it, smem, ps, last, reload)
+                        : batch_item<2, 1, true, false>(p, bi, it, smem, ps, last, reload); break;
+        case 3: ok = q8 ? batch_item<2, 2, false, true>(p, bi, it, smem, ps, last, reload)
+                        : batch_item<2, 2, false, false>(p, bi, it, smem, ps, last, reload); break;
+        default: ok = q8 ? batch_item<2, 2, true, true>(p, bi, it, smem, ps, last, reload)
+                         : batch_item<2, 2, true, false>(p, bi, it, smem, ps, last, reload); break;
+        }
+        if (!ok) break;
+    }
+}
+
+cudaError_t launch_batch(const BatchParams &p, int grid, int smem, cudaStream_t s)
+{
+    static int configured_smem = 0;
+    if (smem > configured_smem) {
+        cudaError_t e = cudaFuncSetAttribute(jdec_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        cudaFuncSetAttribute(jdec_batch_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        configured_smem = smem;
+    }
+    jdec_batch_kernel<<<grid, kCtaThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+int batch_occupancy(int smem)
+{
+    int n = 0;
+    cudaFuncSetAttribute(jdec_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(jdec_batch_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jdec_batch_kernel, kCtaThreads, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
 }
 
 template <int HM, int VM, bool FANCY, bool Q8>

@@ -8,5 +8,7 @@ namespace jdec {
 
 cudaError_t launch_fused(int hm, int vm, bool fancy, const DecodeParams &p, int grid, int smem, cudaStream_t s);
 int fused_occupancy(int hm, int vm, bool fancy, int smem);
+cudaError_t launch_batch(const BatchParams &p, int grid, int smem, cudaStream_t s);
+int batch_occupancy(int smem);
 
 }  // namespace jdec

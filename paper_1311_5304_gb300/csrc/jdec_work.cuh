@@ -148,15 +148,33 @@ __device__ __forceinline__ void fix_edges(uint8_t *slot, int lc, int mx0, int cw
     }
 }
 
-// Runs one work item (MCU rows [r0, r1) of one strip) with the whole CTA.  `smem` is 1024-byte aligned.
-// Returns false if a bounded wait gave up (the error word has been set; the
-// CTA must stop).  `last` = this is the CTA's final item (drain barriers).
+// Runs one work item (MCU rows [r0, r1) of one strip) with the whole CTA.
+// `smem` is 1024-byte aligned; L is the shared-memory layout.  Returns false
+// if a bounded wait gave up (the error word has been set; the CTA must stop).
+// `last` = this is the CTA's final item (drain barriers); `reload_q` = load
+// this image's dequantisation tables first.
+// Writes the dequantisation tables of `d` into shared memory in the layout the
+// IDCT expects (packed bytes for dp2a, or transposed int32).
+template <bool Q8>
+__device__ __forceinline__ void load_qtables(int *qs, const ImageDesc &d, int tid, int nthreads)
+{
+    if (Q8) {
+        // word 64*c + 8*pr + v = Q_c(v, 2pr) | Q_c(v, 2pr+1) << 24
+        for (int i = tid; i < 96; i += nthreads) {
+            const int c = i >> 5, pr = (i >> 3) & 3, v = i & 7;
+            qs[64 * c + 8 * pr + v] = d.q[c][8 * v + 2 * pr] | (d.q[c][8 * v + 2 * pr + 1] << 24);
+        }
+    } else {
+        // qs[64*c + 8*u + v] = Q_c(v, u)
+        for (int i = tid; i < 192; i += nthreads) qs[i] = d.q[i >> 6][((i & 7) << 3) | ((i >> 3) & 7)];
+    }
+}
+
 template <int HM, int VM, bool FANCY, bool Q8>
 __device__ bool run_work(const CUtensorMap *tm, const ImageDesc &d, int strip, int r0, int r1, uint8_t *smem,
-                         PipeState &ps, int *err, bool last)
+                         const SmemLayout &L, PipeState &ps, int *err, bool last, bool reload_q)
 {
     using V = Variant<HM, VM, FANCY>;
-    const SmemLayout L = smem_layout(HM, VM, FANCY, d.wt, d.nslot);
     const int tid = threadIdx.x;
     const int wt = d.wt;
     const int mx0 = strip * wt;
@@ -174,7 +192,12 @@ __device__ bool run_work(const CUtensorMap *tm, const ImageDesc &d, int strip, i
     const int nidct = d.nidct, ncc = kCtaThreads - d.nidct;
     if (tid < nidct) {
         // =================== IDCT warps ===================
-        const int *qs = reinterpret_cast<const int *>(smem + L.off_q);
+        int *qs = reinterpret_cast<int *>(smem + L.off_q);
+        if (reload_q) {
+            // every IDCT thread is past its last use of the previous tables
+            load_qtables<Q8>(qs, d, tid, nidct);
+            named_sync(kBarIdct, nidct);
+        }
         const int lb0 = (V::kHalo && mx0 == 0) ? 1 : 0;
         const int lb1 = min(wte + (V::kHalo ? 2 : 0), d.mcus_x - (mx0 - (V::kHalo ? 1 : 0)));
         const int nce = lb1 - lb0;
@@ -295,8 +318,8 @@ namespace jdec {
 // concatenated strip after strip, split evenly over `nctas` CTAs; `b` is the
 // CTA's index among them.
 template <int HM, int VM, bool FANCY, bool Q8>
-__device__ bool run_share(const CUtensorMap *tm, const ImageDesc &d, int b, uint8_t *smem, PipeState &ps, int *err,
-                          bool last_image)
+__device__ bool run_share(const CUtensorMap *tm, const ImageDesc &d, int b, uint8_t *smem, const SmemLayout &L,
+                          PipeState &ps, int *err, bool last_image)
 {
     const long nrows = d.row1 - d.row0;
     const long total = nrows * d.nstrips;
@@ -307,7 +330,8 @@ __device__ bool run_share(const CUtensorMap *tm, const ImageDesc &d, int b, uint
         const int rr = static_cast<int>(a - s * nrows);
         const int len = static_cast<int>(min(e - a, nrows - rr));
         a += len;
-        if (!run_work<HM, VM, FANCY, Q8>(tm, d, s, d.row0 + rr, d.row0 + rr + len, smem, ps, err, last_image && a >= e))
+        if (!run_work<HM, VM, FANCY, Q8>(tm, d, s, d.row0 + rr, d.row0 + rr + len, smem, L, ps, err,
+                                         last_image && a >= e, false))
             return false;
     }
     return true;

@@ -222,3 +222,57 @@ def encode_jfif(img: CoefImage, restart_interval: int = 0) -> bytes:
         if n <= cap:
             return out[:n].tobytes()
         cap = int(n)
+
+
+# ---- batched workload: many images of mixed size and sampling ----------------
+
+def batch_specs(n: int, seed: int, wmin=160, wmax=4096, hmin=120, hmax=3072,
+                mix=(("420", 0.4), ("422", 0.3), ("444", 0.3)), qrange=(50, 95)):
+    """Sizes, samplings and qualities of an n-image batch: W ~ U[wmin, wmax],
+    H ~ U[hmin, hmax], sampling drawn from `mix`, quality ~ U{qrange}."""
+    rng = np.random.default_rng([seed, 0xBA7C])
+    names = [m[0] for m in mix]
+    probs = np.array([m[1] for m in mix], np.float64)
+    probs /= probs.sum()
+    out = []
+    for _ in range(n):
+        w = int(rng.integers(wmin, wmax + 1))
+        h = int(rng.integers(hmin, hmax + 1))
+        s = str(rng.choice(names, p=probs))
+        q = int(rng.integers(qrange[0], qrange[1] + 1))
+        out.append((w, h, s, q))
+    return out
+
+
+def atlas(sampling: str, width: int = 4096, height: int = 3072, seed: int = 13115304, quality: int = 85) -> CoefImage:
+    """A large textured image whose coefficient planes are cropped into the
+    images of a batch (each crop then gets its own quantisation tables)."""
+    return make_image(width, height, sampling, quality, seed=seed, kind="texture", sigma=4.0, cover=0.85)
+
+
+def crop_offsets(specs, atlases, seed: int):
+    """MCU-aligned crop origin (ox, oy) of every image inside its atlas."""
+    rng = np.random.default_rng([seed, 0xC409])
+    offs = []
+    for (w, h, s, q) in specs:
+        a = atlases[s]
+        hs, vs, mx, my = geometry(w, h, s)
+        _, _, amx, amy = geometry(a.width, a.height, s)
+        offs.append((int(rng.integers(0, amx - mx + 1)), int(rng.integers(0, amy - my + 1))))
+    return offs
+
+
+def crop_planes(planes, sampling, w, h, off):
+    """Crop of atlas coefficient planes (numpy or torch) for a w x h image."""
+    hs, vs, mx, my = geometry(w, h, sampling)
+    ox, oy = off
+    return [planes[c][oy * vs[c]:(oy + my) * vs[c], ox * hs[c]:(ox + mx) * hs[c]] for c in range(3)]
+
+
+def batch_image(specs, atlases, offs, i, fancy=True) -> CoefImage:
+    """Host copy of batch image i (for the oracle)."""
+    w, h, s, q = specs[i]
+    planes = [np.ascontiguousarray(p) for p in crop_planes(atlases[s].planes, s, w, h, offs[i])]
+    hs, vs, _, _ = geometry(w, h, s)
+    qt = [quality_table(q, False), quality_table(q, True), quality_table(q, True)]
+    return CoefImage(w, h, s, hs, vs, planes, qt, fancy, dict(quality=q))
