@@ -1,10 +1,12 @@
 // jdec_batch.cu -- batched decoding of many images with one persistent launch.
 //
 // Host side of jdec_decode_batch: every image is cut into strips of its
-// variant's width; the strips' MCU rows of all images, concatenated image
-// after image, are weighted by their decode cost and split into equal
-// contiguous shares, one per resident CTA (a share becomes a short list of
-// (image, strip, row range) items).  The per-image descriptors (TMA tensor
+// variant's width; for each variant class (sampling, upsampling, 8-bit or
+// 16-bit tables) the strips' MCU rows of its images, concatenated image after
+// image, are weighted by their decode cost and split into equal contiguous
+// shares, one per resident CTA.  A CTA's work list is its share of every
+// class in a fixed class order (a short list of (image, strip, row range)
+// items), so all CTAs of an SM run the same variant's code at a time.  The per-image descriptors (TMA tensor
 // maps, geometry, quantisation tables) and the item lists are written to
 // pinned staging memory and copied to a device buffer that the kernel reads.
 // The copy and the launch are recorded once per launch shape as a CUDA graph
@@ -135,7 +137,7 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
     BatchState *b = ctx->batch;
 
     // ---- per-image strip width and the union of the shared-memory layouts
-    std::vector<int> wt(n), var(n);
+    std::vector<int> wt(n), var(n), q8(n);
     UnionLayout U;
     memset(&U, 0, sizeof(U));
     for (int i = 0; i < n; ++i) {
@@ -143,6 +145,10 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
         int w = tuned_wt(ctx, g);
         wt[i] = std::max(1, std::min(w > 0 ? w : default_wt(g), kMaxWT));
         var[i] = variant_of(g);
+        q8[i] = 1;
+        for (int c = 0; c < 3; ++c)
+            for (int k = 0; k < 64; ++k)
+                if (imgs[i].qtab[c][k] > 255) q8[i] = 0;
         const SmemLayout L = smem_layout(g.hm, g.vm, g.fancy, wt[i], 4);
         U.stage_bytes = std::max(U.stage_bytes, L.stage_bytes);
         U.ybytes = std::max(U.ybytes, L.ybytes);
@@ -157,50 +163,55 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
     const int smem = U.total;
     const int occ = batch_occupancy(smem);
 
-    // ---- cost-balanced split of the concatenated strip-rows
+    // ---- cost-balanced split, one variant class at a time: every CTA gets an
+    // equal share of each class's strip-rows and runs the classes in the same
+    // order, so the CTAs of an SM execute one variant's code at a time.
     struct Seg { int img, strip, rows; double row_cost; };
-    std::vector<Seg> segs;
-    double total = 0.0;
+    std::vector<Seg> segs[10];
+    double total[10] = {0.0};
     long total_rows = 0;
     for (int i = 0; i < n; ++i) {
         const Geometry &g = geo[i];
+        const int cls = 2 * var[i] + (q8[i] ? 1 : 0);
         const int ns = (g.mcus_x + wt[i] - 1) / wt[i];
         for (int st = 0; st < ns; ++st) {
             const int w = std::min(wt[i], g.mcus_x - st * wt[i]);
             const double rc = 64.0 * g.hm * g.vm * w * px_weight(var[i]);
-            segs.push_back(Seg{i, st, g.mcus_y, rc});
-            total += rc * g.mcus_y;
+            segs[cls].push_back(Seg{i, st, g.mcus_y, rc});
+            total[cls] += rc * g.mcus_y;
             total_rows += g.mcus_y;
         }
     }
     const int nctas = static_cast<int>(std::max<long>(1, std::min<long>(static_cast<long>(occ) * ctx->sms, total_rows)));
-    b->items.clear();
-    b->first.assign(nctas + 1, 0);
-    {
-        const double share = total / nctas;
+    std::vector<std::vector<BatchItem>> per_cta(nctas);
+    for (int cls = 0; cls < 10; ++cls) {
+        if (segs[cls].empty()) continue;
+        const double share = total[cls] / nctas;
         int cta = 0;
-        double acc = 0.0;   // cost assigned to CTAs < cta plus the current CTA's part
-        for (const Seg &sg : segs) {
+        double acc = 0.0;   // cost of this class assigned to CTAs < cta plus the current CTA's part
+        for (const Seg &sg : segs[cls]) {
             int r = 0;
             while (r < sg.rows) {
-                // rows this CTA still takes from the segment
                 const double room = (cta + 1) * share - acc;
                 int take = sg.rows - r;
                 if (cta < nctas - 1) {
                     const int fit = static_cast<int>(room / sg.row_cost + 0.5);
                     take = std::max(1, std::min(take, fit));
                 }
-                b->items.push_back(BatchItem{sg.img, sg.strip, r, r + take});
+                per_cta[cta].push_back(BatchItem{sg.img, sg.strip, r, r + take});
                 r += take;
                 acc += take * sg.row_cost;
-                if (cta < nctas - 1 && acc >= (cta + 1) * share - 0.5 * sg.row_cost) {
-                    b->first[++cta] = static_cast<int32_t>(b->items.size());
-                }
+                if (cta < nctas - 1 && acc >= (cta + 1) * share - 0.5 * sg.row_cost) ++cta;
             }
         }
-        const int nitems = static_cast<int>(b->items.size());
-        for (int c = cta + 1; c <= nctas; ++c) b->first[c] = nitems;
     }
+    b->items.clear();
+    b->first.assign(nctas + 1, 0);
+    for (int c = 0; c < nctas; ++c) {
+        b->first[c] = static_cast<int32_t>(b->items.size());
+        b->items.insert(b->items.end(), per_cta[c].begin(), per_cta[c].end());
+    }
+    b->first[nctas] = static_cast<int32_t>(b->items.size());
     const int nitems = static_cast<int>(b->items.size());
 
     // ---- staging layout: images | items | cta_first (fixed offsets per bucket)

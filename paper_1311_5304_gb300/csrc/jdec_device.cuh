@@ -289,9 +289,37 @@ __device__ __forceinline__ int byte_hi16(uint32_t w, int k)
     return static_cast<int>(__byte_perm(w, 0u, 0x4044u | (static_cast<uint32_t>(k) << 8)));
 }
 
+// Writes 24 bytes (little-endian words w[0..5]) to global memory at any
+// alignment: 8-byte stores when the address is 8-byte aligned, 4+8+8+4 bytes
+// at offset 4, else a byte head up to the next 4-byte boundary, five
+// funnel-shifted 4-byte words and a byte tail.  Neighbouring tasks touch
+// disjoint bytes, so the partial words at the ends never race.
+__device__ __forceinline__ void store24(uint8_t *out, const uint32_t w[6])
+{
+    const int a = static_cast<int>(reinterpret_cast<uintptr_t>(out) & 7);
+    if (a == 0) {
+        uint2 *o = reinterpret_cast<uint2 *>(out);
+        o[0] = make_uint2(w[0], w[1]);
+        o[1] = make_uint2(w[2], w[3]);
+        o[2] = make_uint2(w[4], w[5]);
+    } else if (a == 4) {
+        *reinterpret_cast<uint32_t *>(out) = w[0];
+        *reinterpret_cast<uint2 *>(out + 4) = make_uint2(w[1], w[2]);
+        *reinterpret_cast<uint2 *>(out + 12) = make_uint2(w[3], w[4]);
+        *reinterpret_cast<uint32_t *>(out + 20) = w[5];
+    } else {
+        const int s = 4 - (a & 3);          // bytes before the first 4-byte boundary (1..3)
+        const int sh = 8 * s;
+        for (int k = 0; k < s; ++k) out[k] = static_cast<uint8_t>(w[0] >> (8 * k));
+        uint32_t *o = reinterpret_cast<uint32_t *>(out + s);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) o[i] = __funnelshift_r(w[i], w[i + 1], sh);
+        for (int k = s; k < 4; ++k) out[20 + k] = static_cast<uint8_t>(w[5] >> (8 * k));
+    }
+}
+
 // Converts 8 pixels and writes 24 bytes to `out` (global).  yw: the 8 luma
-// samples as two words; `n` = pixels inside the image (1..8); `vec` = the
-// 8-byte vector path is allowed.
+// samples as two words; `n` = pixels inside the image (1..8).
 __device__ __forceinline__ void cc_store8(uint2 yw, const int Cb[8], const int Cr[8], uint8_t *out, int n, bool vec)
 {
     int R[8], G[8], B[8];
@@ -302,11 +330,22 @@ __device__ __forceinline__ void cc_store8(uint2 yw, const int Cb[8], const int C
         G[k] = (ys - Cb[k] * 22554 - Cr[k] * 46802 + 8910336) >> 16;
         B[k] = (ys + Cb[k] * 116130 - 14831872) >> 16;
     }
-    if (vec && n == 8) {
-        uint2 *o = reinterpret_cast<uint2 *>(out);
-        o[0] = make_uint2(pack_sat4(R[0], G[0], B[0], R[1]), pack_sat4(G[1], B[1], R[2], G[2]));
-        o[1] = make_uint2(pack_sat4(B[2], R[3], G[3], B[3]), pack_sat4(R[4], G[4], B[4], R[5]));
-        o[2] = make_uint2(pack_sat4(G[5], B[5], R[6], G[6]), pack_sat4(B[6], R[7], G[7], B[7]));
+    if (n == 8) {
+        uint32_t w[6];
+        w[0] = pack_sat4(R[0], G[0], B[0], R[1]);
+        w[1] = pack_sat4(G[1], B[1], R[2], G[2]);
+        w[2] = pack_sat4(B[2], R[3], G[3], B[3]);
+        w[3] = pack_sat4(R[4], G[4], B[4], R[5]);
+        w[4] = pack_sat4(G[5], B[5], R[6], G[6]);
+        w[5] = pack_sat4(B[6], R[7], G[7], B[7]);
+        if (vec) {
+            uint2 *o = reinterpret_cast<uint2 *>(out);
+            o[0] = make_uint2(w[0], w[1]);
+            o[1] = make_uint2(w[2], w[3]);
+            o[2] = make_uint2(w[4], w[5]);
+        } else {
+            store24(out, w);
+        }
     } else {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {

@@ -46,12 +46,14 @@ __device__ __forceinline__ bool batch_item(const BatchParams &p, const BatchImag
                                            PipeState &ps, bool last, bool reload)
 {
     const SmemLayout L = apply_union(smem_layout(HM, VM, FANCY, bi.desc.wt, 4), p.U);
+    // wt also sizes the layout: read once
     if (reload && threadIdx.x == 0)
         for (int c = 0; c < 3; ++c) {
             tensormap_acquire(&bi.tmap[c]);
             tma_prefetch_map(&bi.tmap[c]);
         }
-    return run_work<HM, VM, FANCY, Q8>(bi.tmap, bi.desc, it.strip, it.r0, it.r1, smem, L, ps, p.err, last, reload);
+    return run_work<HM, VM, FANCY, Q8>(bi.tmap, item_desc(bi.desc), bi.desc, it.strip, it.r0, it.r1, smem, L, ps, p.err,
+                                       last, reload);
 }
 
 //   jdec_batch_kernel: many images of any variants; CTA b runs the items

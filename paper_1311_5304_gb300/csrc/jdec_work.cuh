@@ -25,6 +25,26 @@ namespace jdec {
 
 enum : int { kBarIdct = 1, kBarFull0 = 2, kBarEmpty0 = 4 };
 
+// The per-image values the work loops use, held in registers for the whole
+// item (the batched kernel's descriptors live in global memory).
+struct ItemDesc {
+    uint8_t *rgb;
+    int64_t pitch;
+    int W, H, cw, ch, mcus_x, mcus_y, wt, nidct;
+    bool aligned8;
+};
+
+__device__ __forceinline__ ItemDesc item_desc(const ImageDesc &d)
+{
+    ItemDesc t;
+    t.rgb = d.rgb;
+    t.pitch = d.pitch;
+    t.W = d.W; t.H = d.H; t.cw = d.cw; t.ch = d.ch;
+    t.mcus_x = d.mcus_x; t.mcus_y = d.mcus_y; t.wt = d.wt; t.nidct = d.nidct;
+    t.aligned8 = d.aligned8 != 0;
+    return t;
+}
+
 struct PipeState {
     uint32_t parity;   // bit s = parity of the next completion of stage s
     int job;           // jobs started by this CTA (all items)
@@ -74,14 +94,14 @@ __device__ __forceinline__ void issue_job(const CUtensorMap *tm, const SmemLayou
 // colour warps: one task = 8 pixels of one output row
 // ---------------------------------------------------------------------------
 template <int HM, int VM, bool FANCY>
-__device__ __forceinline__ void cc_task(const ImageDesc &d, const SmemLayout &L, const uint8_t *yplane,
+__device__ __forceinline__ void cc_task(const ItemDesc &d, const SmemLayout &L, const uint8_t *yplane,
                                         const uint8_t *cslots, int job, int r, int mx0, int py, int g)
 {
     const int x0 = (mx0 * HM + g) * 8;
     const int y = r * 8 * VM + py;
     if (x0 >= d.W || y >= d.H) return;
     const int n = min(8, d.W - x0);
-    const bool vec = d.aligned8 != 0;
+    const bool vec = d.aligned8;
     const uint2 yw = *reinterpret_cast<const uint2 *>(yplane + py * L.ypitch + 8 * g);
     int Cb[8], Cr[8];
     if (HM == 1) {
@@ -171,8 +191,8 @@ __device__ __forceinline__ void load_qtables(int *qs, const ImageDesc &d, int ti
 }
 
 template <int HM, int VM, bool FANCY, bool Q8>
-__device__ bool run_work(const CUtensorMap *tm, const ImageDesc &d, int strip, int r0, int r1, uint8_t *smem,
-                         const SmemLayout &L, PipeState &ps, int *err, bool last, bool reload_q)
+__device__ bool run_work(const CUtensorMap *tm, const ItemDesc d, const ImageDesc &qsrc, int strip, int r0, int r1,
+                         uint8_t *smem, const SmemLayout &L, PipeState &ps, int *err, bool last, bool reload_q)
 {
     using V = Variant<HM, VM, FANCY>;
     const int tid = threadIdx.x;
@@ -195,7 +215,7 @@ __device__ bool run_work(const CUtensorMap *tm, const ImageDesc &d, int strip, i
         int *qs = reinterpret_cast<int *>(smem + L.off_q);
         if (reload_q) {
             // every IDCT thread is past its last use of the previous tables
-            load_qtables<Q8>(qs, d, tid, nidct);
+            load_qtables<Q8>(qs, qsrc, tid, nidct);
             named_sync(kBarIdct, nidct);
         }
         const int lb0 = (V::kHalo && mx0 == 0) ? 1 : 0;
@@ -321,6 +341,7 @@ template <int HM, int VM, bool FANCY, bool Q8>
 __device__ bool run_share(const CUtensorMap *tm, const ImageDesc &d, int b, uint8_t *smem, const SmemLayout &L,
                           PipeState &ps, int *err, bool last_image)
 {
+    const ItemDesc id = item_desc(d);
     const long nrows = d.row1 - d.row0;
     const long total = nrows * d.nstrips;
     long a = total * b / d.nctas;
@@ -330,7 +351,7 @@ __device__ bool run_share(const CUtensorMap *tm, const ImageDesc &d, int b, uint
         const int rr = static_cast<int>(a - s * nrows);
         const int len = static_cast<int>(min(e - a, nrows - rr));
         a += len;
-        if (!run_work<HM, VM, FANCY, Q8>(tm, d, s, d.row0 + rr, d.row0 + rr + len, smem, L, ps, err,
+        if (!run_work<HM, VM, FANCY, Q8>(tm, id, d, s, d.row0 + rr, d.row0 + rr + len, smem, L, ps, err,
                                          last_image && a >= e, false))
             return false;
     }
