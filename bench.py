@@ -275,6 +275,8 @@ def run_ours(args, ws, rank, local):
 
     if not args.no_batch:
         out["batch"] = bench_batched(ctx, dev, stream, args.batch_steps, 2)
+    if not args.no_serve:
+        out["serving"] = bench_serving(ctx, dev, [2000, 5000, 10000, 20000, 50000], args.serve_requests, 8.0)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(imgs, args.cpu_seconds)
     if ws > 1:
@@ -333,6 +335,28 @@ def bench_batched(ctx, dev, stream, steps, warmup):
             "plain": {"ms": round(t_plain, 3), "mpix_s": round(px / t_plain / 1e3, 1), "launches": len(descs),
                       "api": "jdec_decode_coeffs per image"},
             "speedup_batched_vs_plain": round(t_plain / t_batch, 3)}
+
+
+def bench_serving(ctx, dev, rates, max_requests, budget_gb):
+    """Config-5 workload: Poisson arrivals, 70% 160x160 / 25% 1920x1080 / 5%
+    4000x3000, all 4:2:0 at quality ~ U{80..92}; HBM budget 8 GB.  Full mode
+    entropy-decodes each JPEG on the host; coefficient mode starts from
+    page-locked coefficient planes.  Latency: arrival -> RGB ready on device."""
+    from paper_1311_5304_gb300 import serve
+    out = {"mix": "70% 160x160, 25% 1920x1080, 5% 4000x3000; 4:2:0 q~U{80..92}", "hbm_budget_gb": budget_gb}
+    for mode in ("full", "coef"):
+        pool = serve.request_pool(13115304 + 5000, mode=mode)
+        srv = serve.Server(ctx, device=dev.index or 0, hbm_budget_bytes=int(budget_gb * (1 << 30)))
+        rows = []
+        try:
+            for rate in rates:
+                n = int(min(max_requests, max(200, rate * 0.5)))
+                rows.append(serve.run_load(srv, pool, rate, n, seed=int(rate), mode=mode, timeout=60))
+        finally:
+            srv.close()
+        out[mode] = rows
+        out["host_threads"] = srv.workers
+    return out
 
 
 def cpu_baseline(imgs, seconds):
@@ -414,6 +438,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--batch-steps", type=int, default=6)
     ap.add_argument("--size", default=f"{SIDE}x{SIDE}", help="WxH of every image of the step")
     ap.add_argument("--variants", default=",".join(VARIANTS), help="samplings decoded per step")

@@ -119,6 +119,29 @@ JDEC_API jdec_status jdec_sync_status(jdec_ctx *ctx, void *stream);
 /* Releases the context and every buffer, graph and tensor map it owns. */
 JDEC_API jdec_status jdec_destroy(jdec_ctx *ctx);
 
+/* ---- Host-side entropy decoding (Sec. 2: the sequential stage; Sec. 4.5:
+ * it runs on the CPU while the GPU back-end works) -------------------------
+ * Baseline (SOF0/SOF1), 8-bit, 3-component, single interleaved scan,
+ * Huffman coding, optional restart intervals.  Thread-safe; no GPU needed. */
+typedef struct {
+    int32_t width, height, ncomp;
+    uint8_t h_samp[3], v_samp[3];
+    int32_t blocks_w[3], blocks_h[3];   /* padded MCU grid, as jdec_image   */
+    uint16_t qtab[3][64];               /* natural order                    */
+    int32_t restart_interval;           /* MCUs per interval, 0 = none      */
+    int64_t scan_offset, scan_bytes;    /* entropy-coded data in the stream */
+} jdec_jpeg_info;
+
+/* Parses the headers of a JPEG stream (no entropy decoding).  Returns
+ * JDEC_EUNSUPPORTED for progressive, arithmetic, 12-bit, or non-3-component
+ * streams and JDEC_EINVAL for malformed ones. */
+JDEC_API jdec_status jdec_jpeg_parse(const uint8_t *data, size_t size, jdec_jpeg_info *info);
+
+/* Huffman-decodes the stream into natural-order int16 coefficient planes laid
+ * out as jdec_image expects (HOST memory, planes[c] holds blocks_w[c] *
+ * blocks_h[c] * 64 int16 as reported by jdec_jpeg_parse). */
+JDEC_API jdec_status jdec_entropy_decode(const uint8_t *data, size_t size, int16_t *const planes[3]);
+
 /* Static description of a status code. */
 JDEC_API const char *jdec_status_str(jdec_status s);
 

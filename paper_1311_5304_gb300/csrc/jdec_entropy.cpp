@@ -1,0 +1,368 @@
+// jdec_entropy.cpp -- host-side baseline JPEG parsing and entropy (Huffman)
+// decoding for the serving path (Sec. 2: the sequential stage that stays on
+// the CPU; Sec. 4.5: it overlaps with the data-parallel back-end).
+//
+// Parsing follows ITU-T T.81 markers (SOI, DQT, SOF0/SOF1, DHT, DRI, SOS).
+// Decoding uses a 64-bit bit buffer refilled a byte at a time (byte stuffing
+// 0xFF00 removed, a marker ends the data) and, per Huffman table, a 9-bit
+// lookahead table giving code length and symbol for short codes, with the
+// canonical MAXCODE/VALPTR search for longer ones.  Coefficients are written
+// in natural order into the component planes (zig-zag undone); restart
+// markers reset the DC predictors.
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "../../include/jdec.h"
+
+namespace {
+
+constexpr int kLook = 9;
+
+struct HuffTable {
+    bool present = false;
+    uint8_t bits[17] = {0};
+    uint8_t vals[256] = {0};
+    int32_t maxcode[18];     // largest code of each length (-1: none), [17] sentinel
+    int32_t valoff[17];      // vals index of the first code of each length minus that code
+    uint16_t look[1 << kLook];   // (length << 8) | symbol, length 0 = not in table
+};
+
+bool build_table(HuffTable &t)
+{
+    int code = 0, k = 0;
+    for (int l = 1; l <= 16; ++l) {
+        t.valoff[l] = k - code;
+        if (t.bits[l]) {
+            code += t.bits[l];
+            k += t.bits[l];
+            t.maxcode[l] = code - 1;
+        } else {
+            t.maxcode[l] = -1;
+        }
+        if (code > (1 << l)) return false;
+        code <<= 1;
+    }
+    t.maxcode[17] = 0x7fffffff;
+    if (k > 256) return false;
+    memset(t.look, 0, sizeof(t.look));
+    code = 0;
+    k = 0;
+    for (int l = 1; l <= kLook; ++l) {
+        for (int i = 0; i < t.bits[l]; ++i, ++k, ++code) {
+            const int shift = kLook - l;
+            for (int f = 0; f < (1 << shift); ++f)
+                t.look[(code << shift) | f] = static_cast<uint16_t>((l << 8) | t.vals[k]);
+        }
+        code <<= 1;
+    }
+    return true;
+}
+
+struct BitReader {
+    const uint8_t *p, *end;
+    uint64_t acc = 0;   // bits are left-aligned: the next bit is bit 63
+    int n = 0;          // valid bits in acc
+    bool marker = false;
+
+    void refill()
+    {
+        while (n <= 56) {
+            uint32_t byte = 0;
+            if (!marker && p < end) {
+                byte = *p;
+                if (byte == 0xFF) {
+                    if (p + 1 < end && p[1] == 0x00) {
+                        p += 2;
+                    } else {
+                        marker = true;   // leave p at the marker
+                        byte = 0;
+                    }
+                } else {
+                    ++p;
+                }
+            }
+            acc |= static_cast<uint64_t>(byte) << (56 - n);
+            n += 8;
+        }
+    }
+    uint32_t peek(int k) { return static_cast<uint32_t>(acc >> (64 - k)); }
+    void skip(int k) { acc <<= k; n -= k; }
+    int get(int k)
+    {
+        if (k == 0) return 0;
+        if (n < k) refill();
+        const int v = static_cast<int>(acc >> (64 - k));
+        skip(k);
+        return v;
+    }
+    void reset_at(const uint8_t *q)
+    {
+        p = q;
+        acc = 0;
+        n = 0;
+        marker = false;
+    }
+    // Byte position of the next unread whole byte (after discarding the bits
+    // left in the buffer): only valid when the buffer holds no more than the
+    // current byte's padding.
+};
+
+inline int decode_symbol(BitReader &br, const HuffTable &t)
+{
+    if (br.n < 16) br.refill();
+    const uint16_t e = t.look[br.peek(kLook)];
+    if (e) {
+        br.skip(e >> 8);
+        return e & 0xff;
+    }
+    int l = kLook + 1;
+    int code = static_cast<int>(br.peek(l));
+    while (l <= 16 && code > t.maxcode[l]) {
+        ++l;
+        code = static_cast<int>(br.peek(l));
+    }
+    if (l > 16) return -1;
+    br.skip(l);
+    return t.vals[t.valoff[l] + code];
+}
+
+inline int extend(int v, int s) { return (s && v < (1 << (s - 1))) ? v - (1 << s) + 1 : v; }
+
+int u16be(const uint8_t *p) { return (p[0] << 8) | p[1]; }
+
+const int *zigzag()
+{
+    static int zz[64];
+    static bool ready = false;
+    if (!ready) {
+        int k = 0;
+        for (int s = 0; s < 15; ++s) {
+            const int lo = s < 8 ? 0 : s - 7, hi = s < 8 ? s : 7;
+            if (s & 1)
+                for (int r = lo; r <= hi; ++r) zz[k++] = r * 8 + (s - r);
+            else
+                for (int r = hi; r >= lo; --r) zz[k++] = r * 8 + (s - r);
+        }
+        ready = true;
+    }
+    return zz;
+}
+
+struct Parsed {
+    jdec_jpeg_info info;
+    HuffTable dc[4], ac[4];
+    int comp_id[3], comp_q[3];
+    int scan_order[3], td[3], ta[3];
+    const uint8_t *scan = nullptr;
+};
+
+jdec_status parse(const uint8_t *data, size_t size, Parsed &P, bool need_tables)
+{
+    const int *zz = zigzag();
+    memset(&P.info, 0, sizeof(P.info));
+    uint16_t qt[4][64];
+    bool qt_present[4] = {false, false, false, false};
+    bool have_sof = false;
+    if (!data || size < 4 || data[0] != 0xFF || data[1] != 0xD8) return JDEC_EINVAL;
+    const uint8_t *p = data + 2, *end = data + size;
+    while (p + 4 <= end) {
+        if (p[0] != 0xFF) return JDEC_EINVAL;
+        const int m = p[1];
+        if (m == 0xFF) {
+            ++p;
+            continue;
+        }
+        if (m == 0xD9) return JDEC_EINVAL;
+        const int len = u16be(p + 2);
+        const uint8_t *s = p + 4, *se = p + 2 + len;
+        if (len < 2 || se > end) return JDEC_EINVAL;
+        if (m == 0xDB) {
+            while (s < se) {
+                const int pq = s[0] >> 4, tq = s[0] & 15;
+                if (tq > 3 || s + 1 + (pq ? 128 : 64) > se) return JDEC_EINVAL;
+                ++s;
+                for (int k = 0; k < 64; ++k) qt[tq][zz[k]] = static_cast<uint16_t>(pq ? u16be(s + 2 * k) : s[k]);
+                s += pq ? 128 : 64;
+                qt_present[tq] = true;
+            }
+        } else if (m == 0xC4) {
+            while (s < se) {
+                const int tc = s[0] >> 4, th = s[0] & 15;
+                if (tc > 1 || th > 3 || s + 17 > se) return JDEC_EINVAL;
+                HuffTable &t = tc ? P.ac[th] : P.dc[th];
+                int total = 0;
+                for (int l = 1; l <= 16; ++l) {
+                    t.bits[l] = s[l];
+                    total += s[l];
+                }
+                if (total > 256 || s + 17 + total > se) return JDEC_EINVAL;
+                memcpy(t.vals, s + 17, static_cast<size_t>(total));
+                if (need_tables && !build_table(t)) return JDEC_EINVAL;
+                t.present = true;
+                s += 17 + total;
+            }
+        } else if (m == 0xC0 || m == 0xC1) {
+            if (len < 8 || s[0] != 8) return JDEC_EUNSUPPORTED;
+            P.info.height = u16be(s + 1);
+            P.info.width = u16be(s + 3);
+            P.info.ncomp = s[5];
+            if (P.info.ncomp != 3) return JDEC_EUNSUPPORTED;
+            if (len < 8 + 9) return JDEC_EINVAL;
+            for (int c = 0; c < 3; ++c) {
+                P.comp_id[c] = s[6 + 3 * c];
+                P.info.h_samp[c] = static_cast<uint8_t>(s[7 + 3 * c] >> 4);
+                P.info.v_samp[c] = static_cast<uint8_t>(s[7 + 3 * c] & 15);
+                P.comp_q[c] = s[8 + 3 * c] & 3;
+                if (P.info.h_samp[c] < 1 || P.info.h_samp[c] > 2 || P.info.v_samp[c] < 1 || P.info.v_samp[c] > 2)
+                    return JDEC_EUNSUPPORTED;
+            }
+            if (P.info.width < 1 || P.info.height < 1) return JDEC_EINVAL;
+            have_sof = true;
+        } else if (m >= 0xC2 && m <= 0xCF && m != 0xC4 && m != 0xC8 && m != 0xCC) {
+            return JDEC_EUNSUPPORTED;   // progressive, lossless, arithmetic coding
+        } else if (m == 0xDD) {
+            if (len < 4) return JDEC_EINVAL;
+            P.info.restart_interval = u16be(s);
+        } else if (m == 0xDA) {
+            if (!have_sof) return JDEC_EINVAL;
+            if (s[0] != 3 || len < 6 + 2 * 3) return JDEC_EUNSUPPORTED;
+            for (int i = 0; i < 3; ++i) {
+                const int id = s[1 + 2 * i];
+                P.scan_order[i] = -1;
+                for (int c = 0; c < 3; ++c)
+                    if (P.comp_id[c] == id) P.scan_order[i] = c;
+                if (P.scan_order[i] < 0) return JDEC_EINVAL;
+                P.td[i] = s[2 + 2 * i] >> 4;
+                P.ta[i] = s[2 + 2 * i] & 15;
+                if (P.td[i] > 3 || P.ta[i] > 3 || !P.dc[P.td[i]].present || !P.ac[P.ta[i]].present) return JDEC_EINVAL;
+            }
+            int hmax = 1, vmax = 1;
+            for (int c = 0; c < 3; ++c) {
+                if (P.info.h_samp[c] > hmax) hmax = P.info.h_samp[c];
+                if (P.info.v_samp[c] > vmax) vmax = P.info.v_samp[c];
+            }
+            const int mx = (P.info.width + 8 * hmax - 1) / (8 * hmax);
+            const int my = (P.info.height + 8 * vmax - 1) / (8 * vmax);
+            for (int c = 0; c < 3; ++c) {
+                P.info.blocks_w[c] = mx * P.info.h_samp[c];
+                P.info.blocks_h[c] = my * P.info.v_samp[c];
+                if (!qt_present[P.comp_q[c]]) return JDEC_EINVAL;
+                memcpy(P.info.qtab[c], qt[P.comp_q[c]], sizeof(P.info.qtab[c]));
+            }
+            P.scan = se;
+            P.info.scan_offset = se - data;
+            P.info.scan_bytes = end - se;
+            return JDEC_OK;
+        }
+        p = se;
+    }
+    return JDEC_EINVAL;
+}
+
+}  // namespace
+
+extern "C" {
+
+JDEC_API jdec_status jdec_jpeg_parse(const uint8_t *data, size_t size, jdec_jpeg_info *info)
+{
+    if (!info) return JDEC_EINVAL;
+    Parsed *P = new (std::nothrow) Parsed();
+    if (!P) return JDEC_ENOMEM;
+    const jdec_status st = parse(data, size, *P, false);
+    if (st == JDEC_OK) *info = P->info;
+    delete P;
+    return st;
+}
+
+JDEC_API jdec_status jdec_entropy_decode(const uint8_t *data, size_t size, int16_t *const planes[3])
+{
+    if (!planes || !planes[0] || !planes[1] || !planes[2]) return JDEC_EINVAL;
+    Parsed *Pp = new (std::nothrow) Parsed();
+    if (!Pp) return JDEC_ENOMEM;
+    Parsed &P = *Pp;
+    jdec_status st = parse(data, size, P, true);
+    if (st != JDEC_OK) {
+        delete Pp;
+        return st;
+    }
+    const int *zz = zigzag();
+    const jdec_jpeg_info &in = P.info;
+    int hmax = 1, vmax = 1;
+    for (int c = 0; c < 3; ++c) {
+        if (in.h_samp[c] > hmax) hmax = in.h_samp[c];
+        if (in.v_samp[c] > vmax) vmax = in.v_samp[c];
+    }
+    const int mx = (in.width + 8 * hmax - 1) / (8 * hmax);
+    const int my = (in.height + 8 * vmax - 1) / (8 * vmax);
+    BitReader br;
+    br.reset_at(P.scan);
+    br.end = data + size;
+    int pred[3] = {0, 0, 0};
+    const long nmcu = static_cast<long>(mx) * my;
+    long todo = in.restart_interval;
+    for (long mcu = 0; mcu < nmcu; ++mcu) {
+        if (in.restart_interval && todo == 0) {
+            // expect RSTn at the marker the reader stopped on
+            const uint8_t *q = br.p;
+            if (!br.marker) {
+                // the reader may have buffered padding bits only; skip to the marker
+                while (q + 1 < br.end && !(q[0] == 0xFF && q[1] != 0x00)) ++q;
+            }
+            if (!(q + 1 < br.end && q[0] == 0xFF && q[1] >= 0xD0 && q[1] <= 0xD7)) {
+                st = JDEC_EINVAL;
+                break;
+            }
+            br.reset_at(q + 2);
+            pred[0] = pred[1] = pred[2] = 0;
+            todo = in.restart_interval;
+        }
+        const int mcx = static_cast<int>(mcu % mx), mcy = static_cast<int>(mcu / mx);
+        for (int i = 0; i < 3 && st == JDEC_OK; ++i) {
+            const int c = P.scan_order[i];
+            const HuffTable &dct = P.dc[P.td[i]], &act = P.ac[P.ta[i]];
+            for (int v = 0; v < in.v_samp[c]; ++v)
+                for (int h = 0; h < in.h_samp[c]; ++h) {
+                    const long bx = static_cast<long>(mcx) * in.h_samp[c] + h;
+                    const long by = static_cast<long>(mcy) * in.v_samp[c] + v;
+                    int16_t *blk = planes[c] + 64 * (by * in.blocks_w[c] + bx);
+                    memset(blk, 0, 64 * sizeof(int16_t));
+                    const int t = decode_symbol(br, dct);
+                    if (t < 0 || t > 11) {
+                        st = JDEC_EINVAL;
+                        break;
+                    }
+                    pred[c] += extend(br.get(t), t);
+                    blk[0] = static_cast<int16_t>(pred[c]);
+                    for (int k = 1; k < 64; ++k) {
+                        const int rs = decode_symbol(br, act);
+                        if (rs < 0) {
+                            st = JDEC_EINVAL;
+                            break;
+                        }
+                        const int r = rs >> 4, s = rs & 15;
+                        if (s == 0) {
+                            if (r == 15) {
+                                k += 15;
+                                continue;
+                            }
+                            break;
+                        }
+                        k += r;
+                        if (k > 63 || s > 10) {
+                            st = JDEC_EINVAL;
+                            break;
+                        }
+                        blk[zz[k]] = static_cast<int16_t>(extend(br.get(s), s));
+                    }
+                    if (st != JDEC_OK) break;
+                }
+        }
+        if (st != JDEC_OK) break;
+        if (in.restart_interval) --todo;
+    }
+    delete Pp;
+    return st;
+}
+
+}  // extern "C"

@@ -29,6 +29,14 @@ class JdecError(RuntimeError):
         super().__init__(f"{what}: {status_str(status)} ({status})")
 
 
+class JpegInfo(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("ncomp", ctypes.c_int32),
+                ("h_samp", ctypes.c_uint8 * 3), ("v_samp", ctypes.c_uint8 * 3),
+                ("blocks_w", ctypes.c_int32 * 3), ("blocks_h", ctypes.c_int32 * 3),
+                ("qtab", (ctypes.c_uint16 * 64) * 3), ("restart_interval", ctypes.c_int32),
+                ("scan_offset", ctypes.c_int64), ("scan_bytes", ctypes.c_int64)]
+
+
 class Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("tune_file", ctypes.c_char_p)]
@@ -83,6 +91,10 @@ def load(build_if_missing: bool = True, path: str | None = None):
         lib.jdec_destroy.restype = ctypes.c_int
         lib.jdec_status_str.argtypes = [ctypes.c_int]
         lib.jdec_status_str.restype = ctypes.c_char_p
+        lib.jdec_jpeg_parse.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(JpegInfo)]
+        lib.jdec_jpeg_parse.restype = ctypes.c_int
+        lib.jdec_entropy_decode.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p * 3)]
+        lib.jdec_entropy_decode.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -93,7 +105,27 @@ def status_str(status: int) -> str:
 
 def exported_symbols() -> list[str]:
     return ["jdec_create", "jdec_decode_coeffs", "jdec_decode_batch", "jdec_decode_host",
-            "jdec_sync_status", "jdec_destroy", "jdec_status_str"]
+            "jdec_sync_status", "jdec_destroy", "jdec_status_str", "jdec_jpeg_parse", "jdec_entropy_decode"]
+
+
+def jpeg_parse(data) -> JpegInfo:
+    """Headers of a baseline JPEG stream (host only)."""
+    buf = data if isinstance(data, (bytes, bytearray)) else bytes(data)
+    info = JpegInfo()
+    st = load().jdec_jpeg_parse(ctypes.c_char_p(bytes(buf)), len(buf), ctypes.byref(info))
+    if st != OK:
+        raise JdecError(st, "jdec_jpeg_parse")
+    return info
+
+
+def entropy_decode(data, planes) -> None:
+    """Huffman-decodes `data` into 3 host int16 planes (numpy arrays or pinned
+    torch CPU tensors) shaped (blocks_h, blocks_w, 64).  Releases the GIL."""
+    ptrs = (ctypes.c_void_p * 3)(*[(p.ctypes.data if isinstance(p, np.ndarray) else p.data_ptr()) for p in planes])
+    buf = data if isinstance(data, bytes) else bytes(data)
+    st = load().jdec_entropy_decode(ctypes.c_char_p(buf), len(buf), ctypes.byref(ptrs))
+    if st != OK:
+        raise JdecError(st, "jdec_entropy_decode")
 
 
 def _stream_ptr(stream) -> int:

@@ -1,0 +1,68 @@
+"""Host entropy decoder of the library (serving path) against the oracle's
+Huffman decoder and the encoder's input planes: identical coefficients."""
+import numpy as np
+import pytest
+
+from paper_1311_5304_gb300 import jdec, synth
+
+
+def _decode(data):
+    info = jdec.jpeg_parse(data)
+    planes = [np.zeros((info.blocks_h[c], info.blocks_w[c], 64), np.int16) for c in range(3)]
+    jdec.entropy_decode(data, planes)
+    return info, planes
+
+
+@pytest.mark.parametrize("sampling", ["444", "422", "420"])
+@pytest.mark.parametrize("restart", [0, 1, 5])
+def test_matches_encoder_and_oracle(orc, sampling, restart):
+    img = synth.make_image(121, 67, sampling, 88, seed=restart + 3, kind="texture", sigma=5)
+    data = synth.encode_jfif(img, restart)
+    info, planes = _decode(data)
+    assert (info.width, info.height) == (121, 67)
+    assert tuple(info.h_samp) == tuple(img.h_samp) and tuple(info.v_samp) == tuple(img.v_samp)
+    assert info.restart_interval == restart
+    oinfo, oplanes = orc.jpeg_decode_coefs(data)
+    for c in range(3):
+        assert np.array_equal(planes[c], img.planes[c])
+        assert np.array_equal(planes[c], oplanes[c])
+        assert np.array_equal(np.array(info.qtab[c][:], np.uint16), img.qtabs[c])
+
+
+def test_dense_coefficients_long_codes_and_stuffing():
+    rng = np.random.default_rng(12)
+    img = synth.random_image(rng, 96, 80, "420")
+    for p in img.planes:
+        p[..., 1:] = rng.integers(-1023, 1024, size=p[..., 1:].shape)
+        p[..., 0] = rng.integers(-1000, 1001, size=p[..., 0].shape)
+    for restart in (0, 3):
+        data = synth.encode_jfif(img, restart)
+        _, planes = _decode(data)
+        for c in range(3):
+            assert np.array_equal(planes[c], img.planes[c])
+
+
+def test_rejects_malformed_and_unsupported():
+    img = synth.make_image(32, 32, "420", 75)
+    data = synth.encode_jfif(img)
+    with pytest.raises(jdec.JdecError):
+        jdec.jpeg_parse(data[:50])
+    with pytest.raises(jdec.JdecError) as e:
+        jdec.jpeg_parse(data.replace(b"\xff\xc0", b"\xff\xc2", 1))   # progressive
+    assert e.value.status == jdec.EUNSUPPORTED
+    info = jdec.jpeg_parse(data)
+    planes = [np.zeros((info.blocks_h[c], info.blocks_w[c], 64), np.int16) for c in range(3)]
+    with pytest.raises(jdec.JdecError):
+        jdec.entropy_decode(data[:200], planes)
+
+
+def test_large_image_throughput_sane():
+    img = synth.make_image(1920, 1080, "420", 85, kind="texture", sigma=4, cover=0.85)
+    data = synth.encode_jfif(img)
+    import time
+    t = time.perf_counter()
+    _, planes = _decode(data)
+    dt = time.perf_counter() - t
+    for c in range(3):
+        assert np.array_equal(planes[c], img.planes[c])
+    assert dt < 2.0
