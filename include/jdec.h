@@ -142,6 +142,23 @@ JDEC_API jdec_status jdec_jpeg_parse(const uint8_t *data, size_t size, jdec_jpeg
  * blocks_h[c] * 64 int16 as reported by jdec_jpeg_parse). */
 JDEC_API jdec_status jdec_entropy_decode(const uint8_t *data, size_t size, int16_t *const planes[3]);
 
+/* Batched decode for callers that cannot allocate device memory (no
+ * counterpart in the paper: a deployment need).  Some callers cannot call
+ * cudaMalloc -- code running while a stream is captured into a CUDA graph,
+ * processes whose device memory is all reserved by another allocator, paths
+ * where the implicit device synchronisation of cudaMalloc/cudaFree is not
+ * acceptable.  This call needs no context and allocates nothing: descriptors,
+ * work list and error word live in one static device array of 512 KiB that
+ * every GPU loading the library holds until exit.  Limits: 1 <= n <= 128
+ * images and a work list of at most 16384 items (about 128 images of 4096
+ * pixels width); larger requests return JDEC_EINVAL and launch nothing.
+ * Results equal jdec_decode_batch.  Runs on the CURRENT device; the first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU race.  Device-side wait timeouts are
+ * recorded in the array, not reported.  Buffers as for jdec_decode_batch. */
+JDEC_API jdec_status jdec_decode_batch_static(const jdec_image *imgs, int32_t n, void *stream);
+
 /* Static description of a status code. */
 JDEC_API const char *jdec_status_str(jdec_status s);
 

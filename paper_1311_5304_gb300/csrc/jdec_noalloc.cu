@@ -1,0 +1,224 @@
+// jdec_noalloc.cu -- jdec_decode_batch_static: the batched decode for callers
+// that cannot allocate device memory.
+//
+// Some callers of a decoder cannot call cudaMalloc: code that runs while a
+// stream is being captured into a CUDA graph (allocation is not allowed
+// during global-mode capture), processes whose device memory is entirely
+// reserved by another allocator (a framework's caching pool holding the
+// whole HBM), and latency-critical paths where cudaMalloc/cudaFree would
+// synchronise the device.  This entry point therefore owns no context and
+// allocates nothing: the per-image descriptors, the work list and the error
+// word live in one file-scope device array, sized below, that every GPU which
+// loads the library holds until the process exits.  Inputs and outputs are
+// still the caller's buffers.
+//
+// The array's name is only a host-side stand-in in host code: the first call
+// on each device (with that device current) asks the runtime for its device
+// address with cudaGetSymbolAddress and keeps it; that first call should come
+// before any stream capture.  Later calls reuse the address.
+//
+// Every call shares the array and it keeps the previous call's contents, so
+// calls whose work overlaps on the GPU (on different streams, or a second call
+// before the first has run) race on it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "jdec_launch.h"
+#include "jdec_runtime.h"
+
+namespace jdec {
+
+// Capacity of the static scratch: 512 KiB holds the header, up to
+// kStaticMaxImages image descriptors, kStaticMaxItems work items and the
+// per-CTA offsets for up to kStaticMaxCtas CTAs.
+constexpr int kStaticMaxImages = 128;
+constexpr int kStaticMaxItems = 16384;
+constexpr int kStaticMaxCtas = 2048;
+constexpr size_t kStaticHeader = 256;                         // error word
+constexpr size_t kStaticImgOff = kStaticHeader;
+constexpr size_t kStaticItemOff = kStaticImgOff + kStaticMaxImages * sizeof(BatchImage);
+constexpr size_t kStaticFirstOff = kStaticItemOff + kStaticMaxItems * sizeof(BatchItem);
+constexpr size_t kStaticBytes = 512 * 1024;
+static_assert(kStaticFirstOff + (kStaticMaxCtas + 1) * sizeof(int32_t) <= kStaticBytes, "static scratch too small");
+
+static __device__ __align__(256) uint8_t g_static_scratch[kStaticBytes];
+
+namespace {
+
+// Host staging of the same layout (static: no heap use per call), guarded by
+// a mutex while a call fills it; the upload copies it before the call returns.
+alignas(256) uint8_t t_host_stage[kStaticBytes];
+Geometry t_geo[kStaticMaxImages];
+int t_cls_items[kStaticMaxCtas];
+std::mutex t_stage_mu;
+
+uint8_t *g_dev_addr[64];   // device address of g_static_scratch per device (null: not set up)
+
+// Cost weights per padded pixel (same ratios as the context-owned batch path).
+double static_px_weight(int variant)
+{
+    static const double w[5] = {1.12, 0.95, 1.05, 0.9, 1.0};
+    return w[variant];
+}
+
+}  // namespace
+
+// Device address of the static scratch on the current device (set-up on the
+// first call per device).
+static jdec_status static_scratch(uint8_t **out, int *device)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return JDEC_ECUDA;
+    if (!g_dev_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return JDEC_ECUDA;
+        }
+        g_dev_addr[dev] = static_cast<uint8_t *>(p);
+    }
+    *out = g_dev_addr[dev];
+    *device = dev;
+    return JDEC_OK;
+}
+
+jdec_status decode_batch_static(const jdec_image *imgs, int n, cudaStream_t s)
+{
+    if (n < 1 || n > kStaticMaxImages || !imgs) return JDEC_EINVAL;
+    std::lock_guard<std::mutex> lock(t_stage_mu);
+    for (int i = 0; i < n; ++i) {
+        jdec_status st = validate(&imgs[i], &t_geo[i], false);
+        if (st != JDEC_OK) return st;
+    }
+    uint8_t *dscratch = nullptr;
+    int device = 0;
+    jdec_status st = static_scratch(&dscratch, &device);
+    if (st != JDEC_OK) return st;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return JDEC_ECUDA;
+
+    // descriptors (default strip widths) and the union layout
+    uint8_t *h = t_host_stage;
+    BatchImage *hi = reinterpret_cast<BatchImage *>(h + kStaticImgOff);
+    UnionLayout U;
+    memset(&U, 0, sizeof(U));
+    for (int i = 0; i < n; ++i) {
+        const Geometry &g = t_geo[i];
+        const int wt = default_wt(g);
+        const SmemLayout L = smem_layout(g.hm, g.vm, g.fancy, wt, 4);
+        U.stage_bytes = std::max(U.stage_bytes, L.stage_bytes);
+        U.ybytes = std::max(U.ybytes, L.ybytes);
+        U.slot_bytes = std::max(U.slot_bytes, L.slot_bytes);
+        BatchImage &bi = hi[i];
+        memset(&bi, 0, sizeof(bi));
+        if (!encode_maps(bi.tmap, &imgs[i], g, wt)) return JDEC_ECUDA;
+        fill_desc(&bi.desc, &imgs[i], g, wt, 1);
+        bi.desc.nslot = 4;
+        bi.desc.nidct = 64;
+        bi.variant = variant_of(g);
+    }
+    U.off_y = kStages * U.stage_bytes;
+    U.off_c = U.off_y + 2 * U.ybytes;
+    U.off_q = U.off_c + 4 * U.slot_bytes;
+    U.off_bar = U.off_q + 3 * 64 * 4;
+    U.off_flag = U.off_bar + 8 * kStages;
+    U.total = U.off_flag + 16 + 1024;
+    const int occ = batch_occupancy(U.total);
+
+    // cost-balanced work list, one variant class after another (as the
+    // context-owned batch path), written straight into the staging image
+    long total_rows = 0;
+    for (int i = 0; i < n; ++i) {
+        const Geometry &g = t_geo[i];
+        total_rows += static_cast<long>((g.mcus_x + hi[i].desc.wt - 1) / hi[i].desc.wt) * g.mcus_y;
+    }
+    const int nctas = static_cast<int>(std::max<long>(
+        1, std::min<long>(std::min<long>(static_cast<long>(occ) * sms, total_rows), kStaticMaxCtas)));
+    BatchItem *items = reinterpret_cast<BatchItem *>(h + kStaticItemOff);
+    int32_t *first = reinterpret_cast<int32_t *>(h + kStaticFirstOff);
+    // pass 1: count items per CTA; pass 2: place them (CTA-major order)
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            int acc = 0;
+            for (int c = 0; c < nctas; ++c) {
+                first[c] = acc;
+                acc += t_cls_items[c];
+                t_cls_items[c] = first[c];   // becomes the write cursor
+            }
+            first[nctas] = acc;
+            if (acc > kStaticMaxItems) return JDEC_EINVAL;   // work list exceeds the static scratch
+        } else {
+            for (int c = 0; c < nctas; ++c) t_cls_items[c] = 0;
+        }
+        for (int cls = 0; cls < 10; ++cls) {
+            double total = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const Geometry &g = t_geo[i];
+                const int q8 = hi[i].desc.q8 ? 1 : 0;
+                if (2 * hi[i].variant + q8 != cls) continue;
+                const int wt = hi[i].desc.wt;
+                const int ns = (g.mcus_x + wt - 1) / wt;
+                for (int stp = 0; stp < ns; ++stp)
+                    total += 64.0 * g.hm * g.vm * std::min(wt, g.mcus_x - stp * wt) * static_px_weight(hi[i].variant) *
+                             g.mcus_y;
+            }
+            if (total <= 0.0) continue;
+            const double share = total / nctas;
+            int cta = 0;
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const Geometry &g = t_geo[i];
+                const int q8 = hi[i].desc.q8 ? 1 : 0;
+                if (2 * hi[i].variant + q8 != cls) continue;
+                const int wt = hi[i].desc.wt;
+                const int ns = (g.mcus_x + wt - 1) / wt;
+                for (int stp = 0; stp < ns; ++stp) {
+                    const double rc = 64.0 * g.hm * g.vm * std::min(wt, g.mcus_x - stp * wt) *
+                                      static_px_weight(hi[i].variant);
+                    int r = 0;
+                    while (r < g.mcus_y) {
+                        int take = g.mcus_y - r;
+                        if (cta < nctas - 1) {
+                            const int fit = static_cast<int>(((cta + 1) * share - acc) / rc + 0.5);
+                            take = std::max(1, std::min(take, fit));
+                        }
+                        if (pass == 0) {
+                            ++t_cls_items[cta];
+                        } else {
+                            items[t_cls_items[cta]++] = BatchItem{i, stp, r, r + take};
+                        }
+                        r += take;
+                        acc += take * rc;
+                        if (cta < nctas - 1 && acc >= (cta + 1) * share - 0.5 * rc) ++cta;
+                    }
+                }
+            }
+        }
+    }
+
+    // upload (pageable host memory: the runtime stages it, nothing is
+    // allocated here), clear the error word, launch
+    const size_t bytes = kStaticFirstOff + static_cast<size_t>(nctas + 1) * sizeof(int32_t);
+    if (cudaMemsetAsync(dscratch, 0, sizeof(int), s) != cudaSuccess) return JDEC_ECUDA;
+    if (cudaMemcpyAsync(dscratch + kStaticImgOff, h + kStaticImgOff, bytes - kStaticImgOff, cudaMemcpyHostToDevice,
+                        s) != cudaSuccess)
+        return JDEC_ECUDA;
+    BatchParams p;
+    p.imgs = reinterpret_cast<const BatchImage *>(dscratch + kStaticImgOff);
+    p.items = reinterpret_cast<const BatchItem *>(dscratch + kStaticItemOff);
+    p.cta_first = reinterpret_cast<const int32_t *>(dscratch + kStaticFirstOff);
+    p.U = U;
+    p.err = reinterpret_cast<int *>(dscratch);
+    if (launch_batch(p, nctas, U.total, s) != cudaSuccess) return JDEC_ECUDA;
+    return JDEC_OK;
+}
+
+}  // namespace jdec
+
+extern "C" JDEC_API jdec_status jdec_decode_batch_static(const jdec_image *imgs, int32_t n, void *stream)
+{
+    return jdec::decode_batch_static(imgs, n, static_cast<cudaStream_t>(stream));
+}

@@ -91,6 +91,8 @@ def load(build_if_missing: bool = True, path: str | None = None):
         lib.jdec_destroy.restype = ctypes.c_int
         lib.jdec_status_str.argtypes = [ctypes.c_int]
         lib.jdec_status_str.restype = ctypes.c_char_p
+        lib.jdec_decode_batch_static.argtypes = [ctypes.POINTER(Image), ctypes.c_int32, P]
+        lib.jdec_decode_batch_static.restype = ctypes.c_int
         lib.jdec_jpeg_parse.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(JpegInfo)]
         lib.jdec_jpeg_parse.restype = ctypes.c_int
         lib.jdec_entropy_decode.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p * 3)]
@@ -105,7 +107,18 @@ def status_str(status: int) -> str:
 
 def exported_symbols() -> list[str]:
     return ["jdec_create", "jdec_decode_coeffs", "jdec_decode_batch", "jdec_decode_host",
-            "jdec_sync_status", "jdec_destroy", "jdec_status_str", "jdec_jpeg_parse", "jdec_entropy_decode"]
+            "jdec_sync_status", "jdec_destroy", "jdec_status_str", "jdec_jpeg_parse", "jdec_entropy_decode",
+            "jdec_decode_batch_static"]
+
+
+def decode_batch_static(imgs, stream=None, check=True) -> int:
+    """Allocation-free batched decode on the current device (see
+    jdec_decode_batch_static in include/jdec.h)."""
+    arr = (Image * len(imgs))(*imgs)
+    st = load().jdec_decode_batch_static(arr, len(imgs), ctypes.c_void_p(_stream_ptr(stream)))
+    if check and st != OK:
+        raise JdecError(st, "jdec_decode_batch_static")
+    return st
 
 
 def jpeg_parse(data) -> JpegInfo:
