@@ -274,7 +274,7 @@ def run_ours(args, ws, rank, local):
            "e2e": e2e, "roofline": roofline, "clocks": clocks, "gpu_launches": len(descs) * K}
 
     if not args.no_batch:
-        out["batch"] = bench_batched(ctx, dev, stream, args.batch_steps, 2)
+        out["batch"] = bench_batched(ctx, dev, stream, args.batch_steps, 2, args.batch_images)
     if not args.no_serve:
         out["serving"] = bench_serving(ctx, dev, [2000, 5000, 10000, 20000, 50000], args.serve_requests, 8.0)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -285,7 +285,7 @@ def run_ours(args, ws, rank, local):
     return out
 
 
-def bench_batched(ctx, dev, stream, steps, warmup):
+def bench_batched(ctx, dev, stream, steps, warmup, nimages=1024):
     """Config-4 workload: 1024 images (W ~ U[160, 4096], H ~ U[120, 3072],
     40/30/30 % 4:2:0 / 4:2:2 / 4:4:4, quality ~ U{50..95}) decoded by one
     batched call (persistent launch, CUDA graph) versus one plain call per
@@ -293,7 +293,7 @@ def bench_batched(ctx, dev, stream, steps, warmup):
     import torch
     from paper_1311_5304_gb300 import jdec, synth
     seed = 13115304 + 4000
-    specs = synth.batch_specs(1024, seed)
+    specs = synth.batch_specs(nimages, seed)
     atl = {sm: synth.atlas(sm, seed=seed + k) for k, sm in enumerate(("420", "422", "444"))}
     offs = synth.crop_offsets(specs, atl, seed)
     dev_atl = {sm: [torch.from_numpy(pl).to(dev) for pl in a.planes] for sm, a in atl.items()}
@@ -327,7 +327,7 @@ def bench_batched(ctx, dev, stream, steps, warmup):
     t_batch = timed(lambda: ctx.decode_batch(descs, stream), steps)
     t_plain = timed(plain, max(1, steps // 2))
     peak = float(measured_peaks()[0]["hbm_gbs"])
-    return {"workload": "1024 images, W~U[160,4096], H~U[120,3072], 40/30/30% 4:2:0/4:2:2/4:4:4, q~U{50..95}",
+    return {"workload": f"{nimages} images, W~U[160,4096], H~U[120,3072], 40/30/30% 4:2:0/4:2:2/4:4:4, q~U{{50..95}}",
             "mpix": round(px / 1e6, 1), "gbytes": round(nbytes / 1e9, 2),
             "batched": {"ms": round(t_batch, 3), "mpix_s": round(px / t_batch / 1e3, 1),
                         "gbs": round(nbytes / t_batch / 1e6, 1), "frac": round(nbytes / t_batch / 1e6 / peak, 4),
@@ -441,6 +441,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--batch-steps", type=int, default=6)
+    ap.add_argument("--batch-images", type=int, default=1024)
     ap.add_argument("--size", default=f"{SIDE}x{SIDE}", help="WxH of every image of the step")
     ap.add_argument("--variants", default=",".join(VARIANTS), help="samplings decoded per step")
     args = ap.parse_args()
