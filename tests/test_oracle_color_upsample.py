@@ -1,7 +1,23 @@
 """Pins for the oracle's colour conversion (Sec. 4.3, Alg. 2) and chroma
 upsampling (Sec. 4.2, Alg. 1 and its 4:2:0 reading)."""
+import os
+
 import numpy as np
 import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rows(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+def alg2_coefficients():
+    """Alg. 2's printed coefficients: ({channel: (cY, cCb, cCr)}, offset)."""
+    rows = _rows("alg2_ycbcr_to_rgb.txt")
+    offset = float(rows[0][1])
+    return {r[0]: tuple(float(v) for v in r[1:4]) for r in rows[1:]}, offset
 
 
 # ---- Alg. 2 ------------------------------------------------------------------
@@ -14,10 +30,11 @@ def cube(orc):
 def test_cc_matches_floating_point_alg2_exhaustively(cube):
     # All 2^24 (Y, Cb, Cr): the 16-bit fixed-point result is within one unit
     # of Alg. 2 evaluated in double precision and rounded (then saturated).
+    coef, offset = alg2_coefficients()
     y = np.arange(256, dtype=np.float64)[:, None, None]
-    cb = np.arange(256, dtype=np.float64)[None, :, None] - 128
-    cr = np.arange(256, dtype=np.float64)[None, None, :] - 128
-    ref = [y + 1.402 * cr, y - 0.34414 * cb - 0.71414 * cr, y + 1.772 * cb]
+    cb = np.arange(256, dtype=np.float64)[None, :, None] - offset
+    cr = np.arange(256, dtype=np.float64)[None, None, :] - offset
+    ref = [coef[ch][0] * y + coef[ch][1] * cb + coef[ch][2] * cr for ch in "RGB"]
     exact = 0
     for c in range(3):
         r = np.clip(np.floor(np.broadcast_to(ref[c], (256, 256, 256)) + 0.5), 0, 255)
@@ -43,17 +60,15 @@ def test_cc_monotone_and_saturating(cube):
 # ---- Alg. 1 (h2v1) ------------------------------------------------------------
 
 def alg1_as_printed(In):
-    """Alg. 1 of the paper for one 8-sample row, written out index by index."""
+    """Alg. 1 of the paper for one 8-sample row, evaluated from its printed
+    index table (tests/golden/alg1_h2v1_upsampling.txt)."""
     i = [int(v) for v in In]
-    return [i[0],
-            (i[0] * 3 + i[1] + 2) // 4, (i[1] * 3 + i[0] + 1) // 4,
-            (i[1] * 3 + i[2] + 2) // 4, (i[2] * 3 + i[1] + 1) // 4,
-            (i[2] * 3 + i[3] + 2) // 4, (i[3] * 3 + i[2] + 1) // 4,
-            (i[3] * 3 + i[4] + 2) // 4, (i[4] * 3 + i[3] + 1) // 4,
-            (i[4] * 3 + i[5] + 2) // 4, (i[5] * 3 + i[4] + 1) // 4,
-            (i[5] * 3 + i[6] + 2) // 4, (i[6] * 3 + i[5] + 1) // 4,
-            (i[6] * 3 + i[7] + 2) // 4, (i[7] * 3 + i[6] + 1) // 4,
-            i[7]]
+    out = [None] * 16
+    for o, c, nb, bias in _rows("alg1_h2v1_upsampling.txt"):
+        o, c = int(o), int(c)
+        out[o] = i[c] if nb == "-" else (3 * i[c] + i[int(nb)] + int(bias)) // 4
+    assert None not in out
+    return out
 
 
 def test_h2v1_fancy_equals_alg1_on_one_block_row(orc):
