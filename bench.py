@@ -57,6 +57,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, ws: int, device=None) -> float:
+    """The slowest rank's time (all ranks call this together)."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mpix_s(px_per_rank_step: float, steps: int, ws: int, ms: float) -> float:
+    """Pixels decoded by all ranks over the slowest rank's time (replicas:
+    every rank decodes its own copy of the step's images)."""
+    return px_per_rank_step * steps * ws / (ms / 1e3) / 1e6
+
+
 def make_workload(size=(SIDE, SIDE), variants=VARIANTS):
     from paper_1311_5304_gb300 import synth
     return [synth.make_image(size[0], size[1], s, QUALITY, seed=SEED, kind="texture", sigma=4.0, cover=0.85,
@@ -207,11 +224,8 @@ def run_ours(args, ws, rank, local):
     elapsed_ms = t_start.elapsed_time(t_end)
     per_var_ms = [statistics.mean(evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(K))
                   for i in range(len(descs))]
-    if ws > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = px_step * K * ws / (elapsed_ms / 1e3) / 1e6
+    elapsed_ms = max_over_ranks(elapsed_ms, ws, dev)
+    value = whole_job_mpix_s(px_step, K, ws, elapsed_ms)
 
     # ---- end to end through the host-buffer entry point ----
     e2e = None
@@ -235,13 +249,11 @@ def run_ours(args, ws, rank, local):
                 ctx.decode_host(d, stream)
         b.record(stream)
         torch.cuda.synchronize(dev)
-        e_ms = a.elapsed_time(b)
         if ws > 1:
-            t = torch.tensor([e_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_ms = float(t.item())
+            torch.distributed.barrier()
+        e_ms = max_over_ranks(a.elapsed_time(b), ws, dev)
         ctx.sync(stream)
-        e2e = {"value": round(px_step * Ke * ws / (e_ms / 1e3) / 1e6, 1), "unit": "MPix/s",
+        e2e = {"value": round(whole_job_mpix_s(px_step, Ke, ws, e_ms), 1), "unit": "MPix/s",
                "h2d_bytes_per_step": int(sum(im.coef_bytes() for im in imgs)),
                "d2h_bytes_per_step": int(sum(im.rgb_bytes() for im in imgs)),
                "steps": Ke, "ms_per_step": round(e_ms / Ke, 3),
