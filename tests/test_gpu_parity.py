@@ -97,6 +97,22 @@ def test_every_strip_width(orc, tmp_path, wt):
             assert_same(got, oracle_rgb(orc, img), f"wt={wt} {sampling} fancy={fancy}")
 
 
+@pytest.mark.parametrize("wt,nidct", [(3, 32), (17, 32), (5, 96), (32, 96)])
+def test_every_warp_split(orc, tmp_path, wt, nidct):
+    # one, two or three IDCT warps (the rest convert colour), forced through a tune file
+    entries = [[v, sc, wt, nidct] for v in range(5) for sc in range(20)]
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    path = tmp_path / "tune.json"
+    path.write_text(json.dumps({"gpu": "x", "sms": sms, "entries": entries}))
+    rng = np.random.default_rng(1000 * wt + nidct)
+    with jdec.Context(tune_file=str(path)) as c:
+        for sampling, fancy in MODES:
+            img = synth.random_image(rng, 517, 263, sampling, fancy=fancy)
+            got, _, _ = gpu_rgb(c, img)
+            assert_same(got, oracle_rgb(orc, img), f"wt={wt} nidct={nidct} {sampling} fancy={fancy}")
+
+
 def test_invalid_descriptions_launch_nothing(ctx):
     import torch
     rng = np.random.default_rng(3)
