@@ -11,7 +11,7 @@ namespace jdec {
 // the strips' MCU rows, concatenated strip after strip, are split into equal
 // contiguous ranges, one per CTA (a range may end one strip and start the
 // next).
-constexpr int kMaxWT = 32;          // widest strip the shared-memory layout allows
+constexpr int kMaxWT = 64;          // widest strip (MCUs) a launch accepts
 constexpr int kStages = 2;          // coefficient double buffer
 
 // Error codes a kernel writes to the context's device error word.

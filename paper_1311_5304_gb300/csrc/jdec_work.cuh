@@ -149,6 +149,47 @@ __device__ __forceinline__ void cc_task(const ItemDesc &d, const SmemLayout &L, 
     cc_store8(yw, Cb, Cr, d.rgb + static_cast<int64_t>(y) * d.pitch + 3 * x0, n, vec);
 }
 
+// 4:2:0 triangular filtering: one task = 8 pixels of the two output rows
+// 2m and 2m+1 of MCU row r, which share the near chroma row j = 8r + m; the
+// far rows are j-1 (row 2m) and j+1 (row 2m+1), clamped to the image.  Chroma
+// block row r lives in slot (job - 1) & 3, the rows above and below it in
+// (job - 2) & 3 and job & 3.
+__device__ __forceinline__ void cc_task_h2v2_pair(const ItemDesc &d, const SmemLayout &L, const uint8_t *yplane,
+                                                  const uint8_t *cslots, int job, int r, int mx0, int m, int g)
+{
+    const int x0 = (2 * mx0 + g) * 8;
+    const int y = 16 * r + 2 * m;
+    if (x0 >= d.W || y >= d.H) return;
+    const int n = min(8, d.W - x0);
+    const bool vec = d.aligned8;
+    const int j = 8 * r + m;
+    const uint8_t *slot = cslots + ((job - 1) & 3) * L.slot_bytes;
+    const uint8_t *pn = slot + m * L.lc + 8 + 4 * g;
+    const uint8_t *pu = m > 0 ? pn - L.lc
+                      : (j > 0 ? cslots + ((job - 2) & 3) * L.slot_bytes + 7 * L.lc + 8 + 4 * g : pn);
+    const uint8_t *pd = j + 1 >= d.ch ? pn
+                      : (m < 7 ? pn + L.lc : cslots + (job & 3) * L.slot_bytes + 8 + 4 * g);
+    const uint2 y0 = *reinterpret_cast<const uint2 *>(yplane + 2 * m * L.ypitch + 8 * g);
+    const uint2 y1 = *reinterpret_cast<const uint2 *>(yplane + (2 * m + 1) * L.ypitch + 8 * g);
+    int Cb0[8], Cr0[8], Cb1[8], Cr1[8];
+    {
+        int n6[6], f6[6];
+        load6(pn, n6);
+        load6(pu, f6);
+        tri_h2v2(n6, f6, Cb0);
+        load6(pd, f6);
+        tri_h2v2(n6, f6, Cb1);
+        load6(pn + 8 * L.lc, n6);
+        load6(pu + 8 * L.lc, f6);
+        tri_h2v2(n6, f6, Cr0);
+        load6(pd + 8 * L.lc, f6);
+        tri_h2v2(n6, f6, Cr1);
+    }
+    uint8_t *out = d.rgb + static_cast<int64_t>(y) * d.pitch + 3 * x0;
+    cc_store8(y0, Cb0, Cr0, out, n, vec);
+    if (y + 1 < d.H) cc_store8(y1, Cb1, Cr1, out + d.pitch, n, vec);
+}
+
 // Replicates the true chroma edge into halo/padding columns of the 8 rows of
 // both components of one chroma slot (strips at the image's left or right
 // edge only, triangular filtering only).  Thread `tid` < 16 does one row.
@@ -304,7 +345,7 @@ __device__ bool run_work(const CUtensorMap *tm, const ItemDesc d, const ImageDes
         // =================== colour warps ===================
         const int tc = tid - nidct;
         const int ngroups = HM * wte;
-        const int rows = 8 * VM;
+        const int rows = V::kRing ? 8 : 8 * VM;   // 4:2:0 triangular: row pairs
         // this thread's first task (row, group) and the per-step advance
         const int py0 = tc / ngroups, g0 = tc - py0 * ngroups;
         const int dpy = ncc / ngroups, dg = ncc - dpy * ngroups;
@@ -317,7 +358,10 @@ __device__ bool run_work(const CUtensorMap *tm, const ItemDesc d, const ImageDes
                 const uint8_t *yplane = yplanes + s * L.ybytes;
                 int py = py0, g = g0;
                 while (py < rows) {
-                    cc_task<HM, VM, FANCY>(d, L, yplane, cslots, j, r, mx0, py, g);
+                    if (V::kRing)
+                        cc_task_h2v2_pair(d, L, yplane, cslots, j, r, mx0, py, g);
+                    else
+                        cc_task<HM, VM, FANCY>(d, L, yplane, cslots, j, r, mx0, py, g);
                     py += dpy;
                     g += dg;
                     if (g >= ngroups) { g -= ngroups; ++py; }

@@ -81,7 +81,7 @@ def test_pitch_and_alignment(ctx, orc, pitch_extra, offset):
         assert_padding_untouched(host, img, pitch, offset)
 
 
-@pytest.mark.parametrize("wt", [1, 2, 3, 5, 8, 13, 17, 32])
+@pytest.mark.parametrize("wt", [1, 2, 3, 5, 8, 13, 17, 32, 42, 64])
 def test_every_strip_width(orc, tmp_path, wt):
     # pin the strip width for every variant and size class through a tune file
     entries = [[v, sc, wt] for v in range(5) for sc in range(20)]
