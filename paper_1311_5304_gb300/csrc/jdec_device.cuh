@@ -370,6 +370,22 @@ __device__ __forceinline__ void load6(const uint8_t *p, int c[6])
     c[5] = byte_of(r, 0);
 }
 
+// Ten samples p[-1 .. 8] around eight chroma centres starting at the 4-byte
+// aligned address p.
+__device__ __forceinline__ void load10(const uint8_t *p, int c[10])
+{
+    const uint32_t l = *reinterpret_cast<const uint32_t *>(p - 4);
+    const uint2 m = *reinterpret_cast<const uint2 *>(p);
+    const uint32_t r = *reinterpret_cast<const uint32_t *>(p + 8);
+    c[0] = byte_of(l, 3);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        c[1 + k] = byte_of(m.x, k);
+        c[5 + k] = byte_of(m.y, k);
+    }
+    c[9] = byte_of(r, 0);
+}
+
 // Alg. 1 (h2v1 triangular) for four centres c[1..4] with neighbours c[0], c[5].
 __device__ __forceinline__ void tri_h2v1(const int c[6], int o[8])
 {

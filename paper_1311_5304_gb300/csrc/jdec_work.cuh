@@ -91,62 +91,62 @@ __device__ __forceinline__ void issue_job(const CUtensorMap *tm, const SmemLayou
 }
 
 // ---------------------------------------------------------------------------
-// colour warps: one task = 8 pixels of one output row
+// colour warps: one task = 16 pixels (two 8-pixel groups) of one output row
 // ---------------------------------------------------------------------------
 template <int HM, int VM, bool FANCY>
 __device__ __forceinline__ void cc_task(const ItemDesc &d, const SmemLayout &L, const uint8_t *yplane,
-                                        const uint8_t *cslots, int job, int r, int mx0, int py, int g)
+                                        const uint8_t *cslots, int job, int r, int mx0, int wte, int py, int gt)
 {
-    const int x0 = (mx0 * HM + g) * 8;
+    const int xg = (mx0 * HM + 2 * gt) * 8;
     const int y = r * 8 * VM + py;
-    if (x0 >= d.W || y >= d.H) return;
-    const int n = min(8, d.W - x0);
+    if (xg >= d.W || y >= d.H) return;
     const bool vec = d.aligned8;
-    const uint2 yw = *reinterpret_cast<const uint2 *>(yplane + py * L.ypitch + 8 * g);
-    int Cb[8], Cr[8];
+    const uint8_t *yrow = yplane + py * L.ypitch + 16 * gt;
+    uint8_t *out = d.rgb + static_cast<int64_t>(y) * d.pitch + 3 * xg;
+    const uint8_t *slot = cslots + (job & (L.nslot - 1)) * L.slot_bytes;
+    int Cb[2][8], Cr[2][8];
     if (HM == 1) {
         // 4:4:4: chroma sample = pixel
-        const uint8_t *cb = cslots + (job & (L.nslot - 1)) * L.slot_bytes + py * L.lc + 8 * g;
+        const uint8_t *cb = slot + py * L.lc + 16 * gt;
+        const uint4 wb = *reinterpret_cast<const uint4 *>(cb);
+        const uint4 wr = *reinterpret_cast<const uint4 *>(cb + 8 * L.lc);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            Cb[0][k] = byte_of(wb.x, k); Cb[0][4 + k] = byte_of(wb.y, k);
+            Cb[1][k] = byte_of(wb.z, k); Cb[1][4 + k] = byte_of(wb.w, k);
+            Cr[0][k] = byte_of(wr.x, k); Cr[0][4 + k] = byte_of(wr.y, k);
+            Cr[1][k] = byte_of(wr.z, k); Cr[1][4 + k] = byte_of(wr.w, k);
+        }
+    } else if (!FANCY) {
+        // replication: chroma sample (x/2, y/VM)
+        const uint8_t *cb = slot + (VM == 2 ? (py >> 1) : py) * L.lc + 8 * gt;
         const uint2 wb = *reinterpret_cast<const uint2 *>(cb);
         const uint2 wr = *reinterpret_cast<const uint2 *>(cb + 8 * L.lc);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            Cb[k] = byte_of(wb.x, k); Cb[4 + k] = byte_of(wb.y, k);
-            Cr[k] = byte_of(wr.x, k); Cr[4 + k] = byte_of(wr.y, k);
+            Cb[0][2 * k] = Cb[0][2 * k + 1] = byte_of(wb.x, k);
+            Cb[1][2 * k] = Cb[1][2 * k + 1] = byte_of(wb.y, k);
+            Cr[0][2 * k] = Cr[0][2 * k + 1] = byte_of(wr.x, k);
+            Cr[1][2 * k] = Cr[1][2 * k + 1] = byte_of(wr.y, k);
         }
-    } else if (!FANCY) {
-        // replication: chroma sample (x/2, y/VM)
-        const uint8_t *cb = cslots + (job & (L.nslot - 1)) * L.slot_bytes + (VM == 2 ? (py >> 1) : py) * L.lc + 4 * g;
-        const uint32_t wb = *reinterpret_cast<const uint32_t *>(cb);
-        const uint32_t wr = *reinterpret_cast<const uint32_t *>(cb + 8 * L.lc);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            Cb[2 * k] = Cb[2 * k + 1] = byte_of(wb, k);
-            Cr[2 * k] = Cr[2 * k + 1] = byte_of(wr, k);
-        }
-    } else if (VM == 1) {
-        // h2v1 triangular (Alg. 1); the slot row starts one halo block left
-        const uint8_t *cb = cslots + (job & (L.nslot - 1)) * L.slot_bytes + py * L.lc + 8 + 4 * g;
-        int c6[6];
-        load6(cb, c6);
-        tri_h2v1(c6, Cb);
-        load6(cb + 8 * L.lc, c6);
-        tri_h2v1(c6, Cr);
     } else {
-        // h2v2 triangular: chroma row j = y/2 (near) and j-1 / j+1 (far, for
-        // even / odd output rows, clamped); chroma block row b lives in slot
-        // (job - 1 + b - r) & 3
-        const int j = y >> 1;
-        const int jf = min(max(j + ((py & 1) ? 1 : -1), 0), d.ch - 1);
-        const uint8_t *pn = cslots + ((job - 1 + (j >> 3) - r) & 3) * L.slot_bytes + (j & 7) * L.lc + 8 + 4 * g;
-        const uint8_t *pf = cslots + ((job - 1 + (jf >> 3) - r) & 3) * L.slot_bytes + (jf & 7) * L.lc + 8 + 4 * g;
-        int n6[6], f6[6];
-        load6(pn, n6); load6(pf, f6);
-        tri_h2v2(n6, f6, Cb);
-        load6(pn + 8 * L.lc, n6); load6(pf + 8 * L.lc, f6);
-        tri_h2v2(n6, f6, Cr);
+        // h2v1 triangular (Alg. 1); the slot row starts one halo block left
+        const uint8_t *cb = slot + py * L.lc + 8 + 8 * gt;
+        int c10[10];
+        load10(cb, c10);
+        tri_h2v1(c10, Cb[0]);
+        tri_h2v1(c10 + 4, Cb[1]);
+        load10(cb + 8 * L.lc, c10);
+        tri_h2v1(c10, Cr[0]);
+        tri_h2v1(c10 + 4, Cr[1]);
     }
-    cc_store8(yw, Cb, Cr, d.rgb + static_cast<int64_t>(y) * d.pitch + 3 * x0, n, vec);
+    const uint2 y0 = *reinterpret_cast<const uint2 *>(yrow);
+    cc_store8(y0, Cb[0], Cr[0], out, min(8, d.W - xg), vec);
+    // the second group may lie past the strip (odd group count) or the image
+    if (2 * gt + 1 < HM * wte && xg + 8 < d.W) {
+        const uint2 y1 = *reinterpret_cast<const uint2 *>(yrow + 8);
+        cc_store8(y1, Cb[1], Cr[1], out + 24, min(8, d.W - xg - 8), vec);
+    }
 }
 
 // 4:2:0 triangular filtering: one task = 8 pixels of the two output rows
@@ -344,8 +344,10 @@ __device__ bool run_work(const CUtensorMap *tm, const ItemDesc d, const ImageDes
     } else {
         // =================== colour warps ===================
         const int tc = tid - nidct;
-        const int ngroups = HM * wte;
-        const int rows = V::kRing ? 8 : 8 * VM;   // 4:2:0 triangular: row pairs
+        // tasks: 4:2:0 triangular, 8 pixels of a pair of output rows; else
+        // 16 pixels of one output row
+        const int ngroups = V::kRing ? HM * wte : (HM * wte + 1) >> 1;
+        const int rows = V::kRing ? 8 : 8 * VM;
         // this thread's first task (row, group) and the per-step advance
         const int py0 = tc / ngroups, g0 = tc - py0 * ngroups;
         const int dpy = ncc / ngroups, dg = ncc - dpy * ngroups;
@@ -361,7 +363,7 @@ __device__ bool run_work(const CUtensorMap *tm, const ItemDesc d, const ImageDes
                     if (V::kRing)
                         cc_task_h2v2_pair(d, L, yplane, cslots, j, r, mx0, py, g);
                     else
-                        cc_task<HM, VM, FANCY>(d, L, yplane, cslots, j, r, mx0, py, g);
+                        cc_task<HM, VM, FANCY>(d, L, yplane, cslots, j, r, mx0, wte, py, g);
                     py += dpy;
                     g += dg;
                     if (g >= ngroups) { g -= ngroups; ++py; }
