@@ -123,12 +123,34 @@ int default_wt(const Geometry &g)
     return g.fancy ? 20 : 21;                 // 6 blocks per MCU (+ 4 halo blocks): 124 / 126
 }
 
+// Strips of (nearly) equal width no wider than `w`: a narrow last strip
+// would leave most of its IDCT and colour threads idle.
+int equal_strips(int mcus_x, int w)
+{
+    const int ns = (mcus_x + w - 1) / w;
+    return (mcus_x + ns - 1) / ns;
+}
+
+// Default strip width of an image whose `nrows` MCU rows are decoded by one
+// launch of up to `wave` CTAs: narrower strips while there are too few
+// strip-rows to give every CTA a few rows (small images), then equal strips.
+static int fit_wt(const Geometry &g, int nrows, long wave)
+{
+    const long min_rows = (g.fancy && g.vm == 2) ? 6 : 2;
+    int w = default_wt(g);
+    while (w > 4 && static_cast<long>((g.mcus_x + w - 1) / w) * nrows < min_rows * wave) w = std::max(4, w / 2);
+    return equal_strips(g.mcus_x, w);
+}
+
 // Strip width (MCUs) and the number of CTAs for `nrows` MCU rows of an image:
 // one full wave (occupancy x SMs) or fewer when there are fewer strip-rows.
 void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int *wt, int *nctas, int *smem)
 {
     int w = force_wt > 0 ? force_wt : tuned_wt(ctx, g);
-    if (w <= 0) w = default_wt(g);
+    if (w <= 0) {
+        const SmemLayout L0 = smem_layout(g.hm, g.vm, g.fancy, default_wt(g), default_slots(g.hm, g.vm, g.fancy));
+        w = fit_wt(g, nrows, static_cast<long>(occupancy_cached(ctx, g.hm, g.vm, g.fancy, L0.total)) * ctx->sms);
+    }
     w = std::max(1, std::min(w, kMaxWT));
     const SmemLayout L = smem_layout(g.hm, g.vm, g.fancy, w, default_slots(g.hm, g.vm, g.fancy));
     const int occ = occupancy_cached(ctx, g.hm, g.vm, g.fancy, L.total);

@@ -1,16 +1,17 @@
-// jdec_batch.cu -- batched decoding of many images with one persistent launch.
+// jdec_batch.cu -- batched decoding of many images in one CUDA graph.
 //
 // Host side of jdec_decode_batch: every image is cut into strips of its
 // variant's width; for each variant class (sampling, upsampling, 8-bit or
 // 16-bit tables) the strips' MCU rows of its images, concatenated image after
 // image, are weighted by their decode cost and split into equal contiguous
-// shares, one per resident CTA.  A CTA's work list is its share of every
-// class in a fixed class order (a short list of (image, strip, row range)
-// items), so all CTAs of an SM run the same variant's code at a time.  The per-image descriptors (TMA tensor
-// maps, geometry, quantisation tables) and the item lists are written to
-// pinned staging memory and copied to a device buffer that the kernel reads.
-// The copy and the launch are recorded once per launch shape as a CUDA graph
-// and replayed for later calls of the same shape.
+// shares, one per resident CTA of that class's kernel.  Each class runs as one
+// persistent launch over its (image, strip, row range) work list, holding
+// only that variant's code; the launches follow each other on the stream.
+// The per-image descriptors (TMA tensor maps, geometry, quantisation tables)
+// and the work lists are written to pinned staging memory and copied to a
+// device buffer that the kernels read.  The copy and the launches are
+// recorded once per launch shape as a CUDA graph and replayed for later calls
+// of the same shape.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -45,11 +46,23 @@ struct MapKeyHash {
     }
 };
 
+// One class launch of a batch: grid, shared memory, layout, and where its
+// per-CTA item offsets start in the staging buffer.
+struct ClassLaunch {
+    int cls, nctas, smem;
+    size_t first_off;
+    UnionLayout U;
+    bool operator==(const ClassLaunch &o) const
+    {
+        return cls == o.cls && nctas == o.nctas && smem == o.smem && first_off == o.first_off &&
+               memcmp(&U, &o.U, sizeof(U)) == 0;
+    }
+};
+
 struct GraphEntry {
     size_t copy_bytes;
-    int nctas, smem;
-    size_t off_items, off_first;
-    UnionLayout U;
+    size_t off_items;
+    std::vector<ClassLaunch> launches;
     cudaGraphExec_t exec;
 };
 
@@ -136,59 +149,69 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
     }
     BatchState *b = ctx->batch;
 
-    // ---- per-image strip width and the union of the shared-memory layouts
-    std::vector<int> wt(n), var(n), q8(n);
-    UnionLayout U;
-    memset(&U, 0, sizeof(U));
+    // ---- per-image strip width, variant class, and per class the union of
+    // its images' shared-memory layouts
+    std::vector<int> wt(n), var(n), cls_of(n);
+    UnionLayout U[10];
+    memset(U, 0, sizeof(U));
     for (int i = 0; i < n; ++i) {
         const Geometry &g = geo[i];
         int w = tuned_wt(ctx, g);
-        wt[i] = std::max(1, std::min(w > 0 ? w : default_wt(g), kMaxWT));
+        wt[i] = std::max(1, std::min(w > 0 ? w : equal_strips(g.mcus_x, default_wt(g)), kMaxWT));
         var[i] = variant_of(g);
-        q8[i] = 1;
+        int q8 = 1;
         for (int c = 0; c < 3; ++c)
             for (int k = 0; k < 64; ++k)
-                if (imgs[i].qtab[c][k] > 255) q8[i] = 0;
+                if (imgs[i].qtab[c][k] > 255) q8 = 0;
+        cls_of[i] = 2 * var[i] + q8;
+        UnionLayout &u = U[cls_of[i]];
         const SmemLayout L = smem_layout(g.hm, g.vm, g.fancy, wt[i], 4);
-        U.stage_bytes = std::max(U.stage_bytes, L.stage_bytes);
-        U.ybytes = std::max(U.ybytes, L.ybytes);
-        U.slot_bytes = std::max(U.slot_bytes, L.slot_bytes);
+        u.stage_bytes = std::max(u.stage_bytes, L.stage_bytes);
+        u.ybytes = std::max(u.ybytes, L.ybytes);
+        u.slot_bytes = std::max(u.slot_bytes, L.slot_bytes);
     }
-    U.off_y = kStages * U.stage_bytes;
-    U.off_c = U.off_y + 2 * U.ybytes;
-    U.off_q = U.off_c + 4 * U.slot_bytes;
-    U.off_bar = U.off_q + 3 * 64 * 4;
-    U.off_flag = U.off_bar + 8 * kStages;
-    U.total = U.off_flag + 16 + 1024;
-    const int smem = U.total;
-    const int occ = batch_occupancy(smem);
+    for (int c = 0; c < 10; ++c) {
+        UnionLayout &u = U[c];
+        u.off_y = kStages * u.stage_bytes;
+        u.off_c = u.off_y + 2 * u.ybytes;
+        u.off_q = u.off_c + 4 * u.slot_bytes;
+        u.off_bar = u.off_q + 3 * 64 * 4;
+        u.off_flag = u.off_bar + 8 * kStages;
+        u.total = u.off_flag + 16 + 1024;
+    }
 
-    // ---- cost-balanced split, one variant class at a time: every CTA gets an
-    // equal share of each class's strip-rows and runs the classes in the same
-    // order, so the CTAs of an SM execute one variant's code at a time.
+    // ---- per class: cost-balanced split of its strip-rows over one wave of
+    // that class's CTAs
     struct Seg { int img, strip, rows; double row_cost; };
     std::vector<Seg> segs[10];
     double total[10] = {0.0};
-    long total_rows = 0;
+    long rows_of[10] = {0};
     for (int i = 0; i < n; ++i) {
         const Geometry &g = geo[i];
-        const int cls = 2 * var[i] + (q8[i] ? 1 : 0);
+        const int cls = cls_of[i];
         const int ns = (g.mcus_x + wt[i] - 1) / wt[i];
         for (int st = 0; st < ns; ++st) {
             const int w = std::min(wt[i], g.mcus_x - st * wt[i]);
             const double rc = 64.0 * g.hm * g.vm * w * px_weight(var[i]);
             segs[cls].push_back(Seg{i, st, g.mcus_y, rc});
             total[cls] += rc * g.mcus_y;
-            total_rows += g.mcus_y;
+            rows_of[cls] += g.mcus_y;
         }
     }
-    const int nctas = static_cast<int>(std::max<long>(1, std::min<long>(static_cast<long>(occ) * ctx->sms, total_rows)));
-    std::vector<std::vector<BatchItem>> per_cta(nctas);
+    std::vector<ClassLaunch> launches;
+    b->items.clear();
+    b->first.clear();
     for (int cls = 0; cls < 10; ++cls) {
         if (segs[cls].empty()) continue;
+        const int smem = U[cls].total;
+        const int occ = batch_class_occupancy(cls, smem);   // also sets the kernel's attributes
+        if (occ <= 0) return JDEC_ECUDA;
+        const int nctas = static_cast<int>(std::max<long>(1, std::min<long>(static_cast<long>(occ) * ctx->sms,
+                                                                            rows_of[cls])));
+        std::vector<std::vector<BatchItem>> per_cta(nctas);
         const double share = total[cls] / nctas;
         int cta = 0;
-        double acc = 0.0;   // cost of this class assigned to CTAs < cta plus the current CTA's part
+        double acc = 0.0;   // cost assigned to CTAs < cta plus the current CTA's part
         for (const Seg &sg : segs[cls]) {
             int r = 0;
             while (r < sg.rows) {
@@ -204,20 +227,20 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
                 if (cta < nctas - 1 && acc >= (cta + 1) * share - 0.5 * sg.row_cost) ++cta;
             }
         }
+        launches.push_back(ClassLaunch{cls, nctas, smem, b->first.size(), U[cls]});
+        for (int c = 0; c < nctas; ++c) {
+            b->first.push_back(static_cast<int32_t>(b->items.size()));
+            b->items.insert(b->items.end(), per_cta[c].begin(), per_cta[c].end());
+        }
+        b->first.push_back(static_cast<int32_t>(b->items.size()));
     }
-    b->items.clear();
-    b->first.assign(nctas + 1, 0);
-    for (int c = 0; c < nctas; ++c) {
-        b->first[c] = static_cast<int32_t>(b->items.size());
-        b->items.insert(b->items.end(), per_cta[c].begin(), per_cta[c].end());
-    }
-    b->first[nctas] = static_cast<int32_t>(b->items.size());
     const int nitems = static_cast<int>(b->items.size());
+    const size_t nfirst = b->first.size();
 
     // ---- staging layout: images | items | cta_first (fixed offsets per bucket)
     const size_t img_bytes = align_up(pow2_at_least(static_cast<size_t>(n), 16) * sizeof(BatchImage), 256);
     const size_t item_bytes = align_up(pow2_at_least(static_cast<size_t>(nitems), 256) * sizeof(BatchItem), 256);
-    const size_t first_bytes = align_up(static_cast<size_t>(nctas + 1) * sizeof(int32_t), 256);
+    const size_t first_bytes = align_up(pow2_at_least(nfirst, 256) * sizeof(int32_t), 256);
     const size_t off_items = img_bytes, off_first = img_bytes + item_bytes;
     const size_t bytes = off_first + first_bytes;
 
@@ -256,30 +279,30 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
         bi.variant = var[i];
     }
     memcpy(h + off_items, b->items.data(), nitems * sizeof(BatchItem));
-    memcpy(h + off_first, b->first.data(), (nctas + 1) * sizeof(int32_t));
+    memcpy(h + off_first, b->first.data(), nfirst * sizeof(int32_t));
 
-    // ---- replay (or record) the copy + launch
+    // ---- replay (or record) the copy + the class launches
     GraphEntry *ge = nullptr;
     for (auto &g : b->graphs)
-        if (g.copy_bytes == bytes && g.nctas == nctas && g.smem == smem && g.off_items == off_items &&
-            g.off_first == off_first && memcmp(&g.U, &U, sizeof(U)) == 0) {
+        if (g.copy_bytes == bytes && g.off_items == off_items && g.launches == launches) {
             ge = &g;
             break;
         }
     if (!ge) {
         if (b->graphs.size() >= 64) drop_graphs(b);
-        BatchParams p;
-        p.imgs = static_cast<const BatchImage *>(b->d_buf);
-        p.items = reinterpret_cast<const BatchItem *>(static_cast<uint8_t *>(b->d_buf) + off_items);
-        p.cta_first = reinterpret_cast<const int32_t *>(static_cast<uint8_t *>(b->d_buf) + off_first);
-        p.U = U;
-        p.err = ctx->d_err;
-        // make sure the kernel attributes are set outside the capture
-        if (batch_occupancy(smem) <= 0) return JDEC_ECUDA;
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return JDEC_ECUDA;
         cudaError_t e1 = cudaMemcpyAsync(b->d_buf, b->h_buf, bytes, cudaMemcpyHostToDevice, b->cap_stream);
-        cudaError_t e2 = launch_batch(p, nctas, smem, b->cap_stream);
+        cudaError_t e2 = cudaSuccess;
+        for (const ClassLaunch &cl : launches) {
+            BatchParams p;
+            p.imgs = static_cast<const BatchImage *>(b->d_buf);
+            p.items = reinterpret_cast<const BatchItem *>(static_cast<uint8_t *>(b->d_buf) + off_items);
+            p.cta_first = reinterpret_cast<const int32_t *>(static_cast<uint8_t *>(b->d_buf) + off_first) + cl.first_off;
+            p.U = cl.U;
+            p.err = ctx->d_err;
+            if (e2 == cudaSuccess) e2 = launch_batch_class(cl.cls, p, cl.nctas, cl.smem, b->cap_stream);
+        }
         cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &graph);
         if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || !graph) {
             if (graph) cudaGraphDestroy(graph);
@@ -293,12 +316,12 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
             cudaGetLastError();
             return JDEC_ECUDA;
         }
-        b->graphs.push_back(GraphEntry{bytes, nctas, smem, off_items, off_first, U, exec});
+        b->graphs.push_back(GraphEntry{bytes, off_items, launches, exec});
         ge = &b->graphs.back();
     }
     if (cudaGraphLaunch(ge->exec, s) != cudaSuccess) return JDEC_ECUDA;
     if (cudaEventRecord(b->copied, s) == cudaSuccess) b->copy_pending = true;
-    ctx->launches++;
+    ctx->launches += static_cast<long>(launches.size());
     return JDEC_OK;
 }
 

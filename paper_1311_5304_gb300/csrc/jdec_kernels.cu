@@ -22,6 +22,29 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p)
     return reinterpret_cast<uint8_t *>((a + 1023) & ~static_cast<uintptr_t>(1023));
 }
 
+// Raises a kernel's dynamic shared-memory limit to the device's opt-in
+// maximum and prefers the largest shared-memory carveout, once per kernel and
+// device (`done` has one flag per device ordinal).  Occupancy queries and
+// launches of every size then see the same attribute.
+struct ConfigFlags {
+    bool done[64] = {};
+};
+
+template <typename K>
+static cudaError_t configure_kernel(K k, ConfigFlags &f)
+{
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && f.done[dev]) return cudaSuccess;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) f.done[dev] = true;
+    return e;
+}
+
 template <int HM, int VM, bool FANCY, bool Q8>
 __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_fused_kernel(const __grid_constant__ DecodeParams p)
 {
@@ -96,26 +119,106 @@ __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_batch_kernel(
     }
 }
 
+//   jdec_batch_class_kernel<HM, VM, FANCY, Q8>: the same work-list walk for
+//     the items of one variant class only, so each launch holds one variant's
+//     code (no instruction-cache competition between variants, registers
+//     allocated for that variant alone).
+template <int HM, int VM, bool FANCY, bool Q8>
+__global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS)
+    jdec_batch_class_kernel(const __grid_constant__ BatchParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = align1024(smem_raw);
+    if (threadIdx.x == 0) {
+        *reinterpret_cast<volatile int *>(smem + p.U.off_flag) = 0;
+        for (int s = 0; s < kStages; ++s) mbar_init(smem_u32(smem + p.U.off_bar + 8 * s), 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    PipeState ps{0u, 0};
+    const int i0 = p.cta_first[blockIdx.x], i1 = p.cta_first[blockIdx.x + 1];
+    int cur = -1;
+    for (int i = i0; i < i1; ++i) {
+        const BatchItem it = p.items[i];
+        const BatchImage &bi = p.imgs[it.img];
+        const bool reload = it.img != cur;
+        cur = it.img;
+        if (!batch_item<HM, VM, FANCY, Q8>(p, bi, it, smem, ps, i + 1 == i1, reload)) break;
+    }
+}
+
+template <int HM, int VM, bool FANCY, bool Q8>
+static cudaError_t launch_class_t(const BatchParams &p, int grid, int smem, cudaStream_t s)
+{
+    auto k = jdec_batch_class_kernel<HM, VM, FANCY, Q8>;
+    static ConfigFlags configured;
+    cudaError_t e = configure_kernel(k, configured);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kCtaThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int HM, int VM, bool FANCY, bool Q8>
+static int occupancy_class_t(int smem)
+{
+    int n = 0;
+    auto k = jdec_batch_class_kernel<HM, VM, FANCY, Q8>;
+    static ConfigFlags configured;
+    if (configure_kernel(k, configured) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kCtaThreads, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+// Class = 2 * variant + q8 (variant 0: 4:4:4, 1: 4:2:2 replicate, 2: 4:2:2
+// triangular, 3: 4:2:0 replicate, 4: 4:2:0 triangular).
+cudaError_t launch_batch_class(int cls, const BatchParams &p, int grid, int smem, cudaStream_t s)
+{
+    switch (cls) {
+    case 0: return launch_class_t<1, 1, false, false>(p, grid, smem, s);
+    case 1: return launch_class_t<1, 1, false, true>(p, grid, smem, s);
+    case 2: return launch_class_t<2, 1, false, false>(p, grid, smem, s);
+    case 3: return launch_class_t<2, 1, false, true>(p, grid, smem, s);
+    case 4: return launch_class_t<2, 1, true, false>(p, grid, smem, s);
+    case 5: return launch_class_t<2, 1, true, true>(p, grid, smem, s);
+    case 6: return launch_class_t<2, 2, false, false>(p, grid, smem, s);
+    case 7: return launch_class_t<2, 2, false, true>(p, grid, smem, s);
+    case 8: return launch_class_t<2, 2, true, false>(p, grid, smem, s);
+    case 9: return launch_class_t<2, 2, true, true>(p, grid, smem, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int batch_class_occupancy(int cls, int smem)
+{
+    switch (cls) {
+    case 0: return occupancy_class_t<1, 1, false, false>(smem);
+    case 1: return occupancy_class_t<1, 1, false, true>(smem);
+    case 2: return occupancy_class_t<2, 1, false, false>(smem);
+    case 3: return occupancy_class_t<2, 1, false, true>(smem);
+    case 4: return occupancy_class_t<2, 1, true, false>(smem);
+    case 5: return occupancy_class_t<2, 1, true, true>(smem);
+    case 6: return occupancy_class_t<2, 2, false, false>(smem);
+    case 7: return occupancy_class_t<2, 2, false, true>(smem);
+    case 8: return occupancy_class_t<2, 2, true, false>(smem);
+    case 9: return occupancy_class_t<2, 2, true, true>(smem);
+    default: return 0;
+    }
+}
+
 cudaError_t launch_batch(const BatchParams &p, int grid, int smem, cudaStream_t s)
 {
-    static int configured_smem = 0;
-    if (smem > configured_smem) {
-        cudaError_t e = cudaFuncSetAttribute(jdec_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        cudaFuncSetAttribute(jdec_batch_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        configured_smem = smem;
-    }
+    static ConfigFlags configured;
+    cudaError_t e = configure_kernel(jdec_batch_kernel, configured);
+    if (e != cudaSuccess) return e;
     jdec_batch_kernel<<<grid, kCtaThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 int batch_occupancy(int smem)
 {
+    static ConfigFlags configured;
     int n = 0;
-    cudaFuncSetAttribute(jdec_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(jdec_batch_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxShared);
+    if (configure_kernel(jdec_batch_kernel, configured) != cudaSuccess) return 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jdec_batch_kernel, kCtaThreads, smem) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }
@@ -124,13 +227,9 @@ template <int HM, int VM, bool FANCY, bool Q8>
 static cudaError_t launch_variant(const DecodeParams &p, int grid, int smem, cudaStream_t s)
 {
     auto k = jdec_fused_kernel<HM, VM, FANCY, Q8>;
-    static int configured_smem = 0;
-    if (smem > configured_smem) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-        configured_smem = smem;
-    }
+    static ConfigFlags configured;
+    cudaError_t e = configure_kernel(k, configured);
+    if (e != cudaSuccess) return e;
     k<<<grid, kCtaThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
@@ -154,8 +253,8 @@ static int occupancy_variant(int smem)
 {
     int n = 0;
     auto k = jdec_fused_kernel<HM, VM, FANCY, true>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    static ConfigFlags configured;
+    if (configure_kernel(k, configured) != cudaSuccess) return 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kCtaThreads, smem) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }

@@ -10,5 +10,7 @@ cudaError_t launch_fused(int hm, int vm, bool fancy, const DecodeParams &p, int 
 int fused_occupancy(int hm, int vm, bool fancy, int smem);
 cudaError_t launch_batch(const BatchParams &p, int grid, int smem, cudaStream_t s);
 int batch_occupancy(int smem);
+cudaError_t launch_batch_class(int cls, const BatchParams &p, int grid, int smem, cudaStream_t s);
+int batch_class_occupancy(int cls, int smem);   // 0 if the class cannot be resident
 
 }  // namespace jdec

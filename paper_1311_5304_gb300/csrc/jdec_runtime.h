@@ -74,6 +74,7 @@ jdec_status ensure_buffer(jdec_ctx *ctx, void **buf, size_t *cap, size_t need);
 
 int variant_of(const Geometry &g);
 int default_wt(const Geometry &g);
+int equal_strips(int mcus_x, int w);   // widest equal strips no wider than w
 int size_class_of(const Geometry &g);
 int tuned_wt(jdec_ctx *ctx, const Geometry &g);
 int tuned_nidct(jdec_ctx *ctx, const Geometry &g);
