@@ -289,32 +289,69 @@ __device__ __forceinline__ int byte_hi16(uint32_t w, int k)
     return static_cast<int>(__byte_perm(w, 0u, 0x4044u | (static_cast<uint32_t>(k) << 8)));
 }
 
+// Bytes [i, i+4) and [i, i+2) of the 24 little-endian bytes in w (i a
+// compile-time constant after inlining).
+__device__ __forceinline__ uint32_t bytes32(const uint32_t w[6], int i)
+{
+    return (i & 3) ? __funnelshift_r(w[i >> 2], w[(i >> 2) + 1], 8 * (i & 3)) : w[i >> 2];
+}
+__device__ __forceinline__ uint16_t bytes16(const uint32_t w[6], int i)
+{
+    return static_cast<uint16_t>((i & 3) == 3 ? __funnelshift_r(w[i >> 2], w[(i >> 2) + 1], 24) : w[i >> 2] >> (8 * (i & 3)));
+}
+
+// Writes 24 bytes to `out` with out % 8 == A (1..7): naturally aligned 1-,
+// 2- and 4-byte stores up to the 8-byte boundary, two 8-byte stores, then
+// the A remaining bytes with 4-, 2- and 1-byte stores.
+template <int A>
+__device__ __forceinline__ void store24_at(uint8_t *out, const uint32_t w[6])
+{
+    constexpr int S = 8 - A;   // bytes below the first 8-byte boundary
+    int o = 0;
+    if (S & 1) {
+        out[0] = static_cast<uint8_t>(w[0]);
+        o = 1;
+    }
+    if ((S - o) & 2) {
+        *reinterpret_cast<uint16_t *>(out + o) = bytes16(w, o);
+        o += 2;
+    }
+    if (S - o >= 4) *reinterpret_cast<uint32_t *>(out + o) = bytes32(w, o);
+    reinterpret_cast<uint2 *>(out + S)[0] = make_uint2(bytes32(w, S), bytes32(w, S + 4));
+    reinterpret_cast<uint2 *>(out + S)[1] = make_uint2(bytes32(w, S + 8), bytes32(w, S + 12));
+    int t = S + 16;
+    if (A & 4) {
+        *reinterpret_cast<uint32_t *>(out + t) = bytes32(w, t);
+        t += 4;
+    }
+    if (A & 2) {
+        *reinterpret_cast<uint16_t *>(out + t) = bytes16(w, t);
+        t += 2;
+    }
+    if (A & 1) out[t] = static_cast<uint8_t>(w[5] >> 24);
+}
+
 // Writes 24 bytes (little-endian words w[0..5]) to global memory at any
-// alignment: 8-byte stores when the address is 8-byte aligned, 4+8+8+4 bytes
-// at offset 4, else a byte head up to the next 4-byte boundary, five
-// funnel-shifted 4-byte words and a byte tail.  Neighbouring tasks touch
-// disjoint bytes, so the partial words at the ends never race.
+// alignment with naturally aligned stores (three 8-byte stores when out is
+// 8-byte aligned).  Neighbouring tasks touch disjoint bytes, so the partial
+// words at the ends never race.
 __device__ __forceinline__ void store24(uint8_t *out, const uint32_t w[6])
 {
-    const int a = static_cast<int>(reinterpret_cast<uintptr_t>(out) & 7);
-    if (a == 0) {
+    switch (static_cast<int>(reinterpret_cast<uintptr_t>(out) & 7)) {
+    case 0: {
         uint2 *o = reinterpret_cast<uint2 *>(out);
         o[0] = make_uint2(w[0], w[1]);
         o[1] = make_uint2(w[2], w[3]);
         o[2] = make_uint2(w[4], w[5]);
-    } else if (a == 4) {
-        *reinterpret_cast<uint32_t *>(out) = w[0];
-        *reinterpret_cast<uint2 *>(out + 4) = make_uint2(w[1], w[2]);
-        *reinterpret_cast<uint2 *>(out + 12) = make_uint2(w[3], w[4]);
-        *reinterpret_cast<uint32_t *>(out + 20) = w[5];
-    } else {
-        const int s = 4 - (a & 3);          // bytes before the first 4-byte boundary (1..3)
-        const int sh = 8 * s;
-        for (int k = 0; k < s; ++k) out[k] = static_cast<uint8_t>(w[0] >> (8 * k));
-        uint32_t *o = reinterpret_cast<uint32_t *>(out + s);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) o[i] = __funnelshift_r(w[i], w[i + 1], sh);
-        for (int k = s; k < 4; ++k) out[20 + k] = static_cast<uint8_t>(w[5] >> (8 * k));
+        break;
+    }
+    case 1: store24_at<1>(out, w); break;
+    case 2: store24_at<2>(out, w); break;
+    case 3: store24_at<3>(out, w); break;
+    case 4: store24_at<4>(out, w); break;
+    case 5: store24_at<5>(out, w); break;
+    case 6: store24_at<6>(out, w); break;
+    default: store24_at<7>(out, w); break;
     }
 }
 
