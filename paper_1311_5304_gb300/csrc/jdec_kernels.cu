@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_fused_kernel(
         for (int c = 0; c < 3; ++c) tma_prefetch_map(&p.tmap[c]);
     }
     __syncthreads();
-    PipeState ps{0u, 0};
+    PipeState ps{0u, 0, 0};
     run_share<HM, VM, FANCY, Q8>(p.tmap, p.img, blockIdx.x, smem, L, ps, p.err, true);
 }
 
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_batch_kernel(
         fence_barrier_init();
     }
     __syncthreads();
-    PipeState ps{0u, 0};
+    PipeState ps{0u, 0, 0};
     const int i0 = p.cta_first[blockIdx.x], i1 = p.cta_first[blockIdx.x + 1];
     int cur = -1;
     for (int i = i0; i < i1; ++i) {
@@ -100,7 +100,9 @@ __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_batch_kernel(
         const BatchImage &bi = p.imgs[it.img];
         const bool reload = it.img != cur;
         cur = it.img;
-        const bool last = i + 1 == i1;
+        // items of different variants may use different warp roles: every
+        // split-role item drains its barriers
+        const bool last = true;
         bool ok;
         const bool q8 = bi.desc.q8 != 0;
         switch (bi.variant) {
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS)
         fence_barrier_init();
     }
     __syncthreads();
-    PipeState ps{0u, 0};
+    PipeState ps{0u, 0, 0};
     const int i0 = p.cta_first[blockIdx.x], i1 = p.cta_first[blockIdx.x + 1];
     int cur = -1;
     for (int i = i0; i < i1; ++i) {

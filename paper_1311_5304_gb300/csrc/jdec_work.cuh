@@ -48,6 +48,7 @@ __device__ __forceinline__ ItemDesc item_desc(const ImageDesc &d)
 struct PipeState {
     uint32_t parity;   // bit s = parity of the next completion of stage s
     int job;           // jobs started by this CTA (all items)
+    int sync_from;     // first job whose colour warps signal EMPTY (split roles)
 };
 
 template <int HM, int VM, bool FANCY>
@@ -56,6 +57,9 @@ struct Variant {
     static constexpr bool kRing = FANCY && HM == 2 && VM == 2; // vertical neighbours
     static constexpr int kLA = kRing ? 1 : 0;                  // chroma lookahead rows
     static constexpr int kPro = kRing ? 2 : 0;                 // chroma-only jobs per item
+    // every warp transforms and then converts each job (triangular 4:2:2 and
+    // 4:2:0, where colour work is close to IDCT work); else split warp roles
+    static constexpr bool kUnified = FANCY && HM == 2;
 };
 
 // Job k of an item covering MCU rows [r0, r1): its luma row (-1: none) and
@@ -232,8 +236,9 @@ __device__ __forceinline__ void load_qtables(int *qs, const ImageDesc &d, int ti
 }
 
 template <int HM, int VM, bool FANCY, bool Q8>
-__device__ bool run_work(const CUtensorMap *tm, const ItemDesc d, const ImageDesc &qsrc, int strip, int r0, int r1,
-                         uint8_t *smem, const SmemLayout &L, PipeState &ps, int *err, bool last, bool reload_q)
+__device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const ImageDesc &qsrc, int strip, int r0,
+                               int r1, uint8_t *smem, const SmemLayout &L, PipeState &ps, int *err, bool last,
+                               bool reload_q)
 {
     using V = Variant<HM, VM, FANCY>;
     const int tid = threadIdx.x;
@@ -281,7 +286,7 @@ __device__ bool run_work(const CUtensorMap *tm, const ItemDesc d, const ImageDes
             int yrow, crow;
             job_rows<HM, VM, FANCY>(k, r0, yrow, crow);
             const bool do_c = crow >= 0 && crow < d.mcus_y;
-            if (j >= 2) named_sync(kBarEmpty0 + s, kCtaThreads);
+            if (j >= ps.sync_from + 2) named_sync(kBarEmpty0 + s, kCtaThreads);
             const bool ok = mbar_wait_bounded(bar0 + 8 * s, (ps.parity >> s) & 1u, budget);
             ps.parity ^= 1u << s;
             if (!ok) *abort_flag = 1;
@@ -339,7 +344,8 @@ __device__ bool run_work(const CUtensorMap *tm, const ItemDesc d, const ImageDes
             // consume the colour warps' EMPTY signals of the final two jobs, as
             // jobs ps.job and ps.job + 1 would
             for (int jj = ps.job; jj < ps.job + 2; ++jj)
-                if (jj >= 2) named_sync(kBarEmpty0 + (jj & 1), kCtaThreads);
+                if (jj >= ps.sync_from + 2) named_sync(kBarEmpty0 + (jj & 1), kCtaThreads);
+            ps.sync_from = ps.job;
         }
     } else {
         // =================== colour warps ===================
@@ -353,6 +359,9 @@ __device__ bool run_work(const CUtensorMap *tm, const ItemDesc d, const ImageDes
         const int dpy = ncc / ngroups, dg = ncc - dpy * ngroups;
         for (int k = 0; k < njobs; ++k) {
             const int j = J0 + k, s = j & 1;
+            // keep this thread's copy of the stage parities in step with the
+            // IDCT warps' (a unified-role item may follow)
+            ps.parity ^= 1u << s;
             named_sync(kBarFull0 + s, kCtaThreads);
             if (*abort_flag) return false;
             if (k >= V::kPro) {
@@ -372,8 +381,160 @@ __device__ bool run_work(const CUtensorMap *tm, const ItemDesc d, const ImageDes
             named_arrive(kBarEmpty0 + s, kCtaThreads);
         }
         ps.job = J0 + njobs;
+        if (last) ps.sync_from = ps.job;
     }
     return true;
+}
+
+// Unified roles: every thread takes part in both halves of every job k:
+//   wait for job k's TMA tile; IDCT tasks of job k; CTA barrier;
+//   (thread 0 refills the consumed stage with job k+2; edge strips replicate
+//   the true chroma edge, then a second barrier); colour tasks of job k.
+// One barrier per job suffices: a thread that starts the IDCT of job k+1 may
+// overlap slower threads' colour tasks of job k because luma planes are
+// double-buffered and chroma slots rotate (job k+1 writes neither the plane
+// nor the slots that job k reads), and a thread that starts job k+2 has passed
+// the barrier of job k+1, which every thread reaches only after finishing the
+// colour tasks of job k.  No named barrier is left half-signalled, so an item
+// of either kind may follow.
+template <int HM, int VM, bool FANCY, bool Q8>
+__device__ bool run_work_unified(const CUtensorMap *tm, const ItemDesc d, const ImageDesc &qsrc, int strip, int r0,
+                                 int r1, uint8_t *smem, const SmemLayout &L, PipeState &ps, int *err, bool reload_q)
+{
+    using V = Variant<HM, VM, FANCY>;
+    const int tid = threadIdx.x;
+    const int wt = d.wt;
+    const int mx0 = strip * wt;
+    const int wte = min(wt, d.mcus_x - mx0);
+    if (r0 >= r1 || wte <= 0) return true;
+    const int njobs = V::kPro + (r1 - r0);
+    const int J0 = ps.job;
+
+    uint8_t *stages = smem + L.off_stage;
+    uint8_t *yplanes = smem + L.off_y;
+    uint8_t *cslots = smem + L.off_c;
+    const uint32_t bar0 = smem_u32(smem + L.off_bar);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L.off_flag);
+    int *qs = reinterpret_cast<int *>(smem + L.off_q);
+    if (reload_q) {
+        // every thread is past the barrier that follows the previous item's
+        // last IDCT tasks, so nobody reads the old tables any more
+        load_qtables<Q8>(qs, qsrc, tid, kCtaThreads);
+        __syncthreads();
+    }
+    const int lb0 = (V::kHalo && mx0 == 0) ? 1 : 0;
+    const int lb1 = min(wte + (V::kHalo ? 2 : 0), d.mcus_x - (mx0 - (V::kHalo ? 1 : 0)));
+    const int nce = lb1 - lb0;
+    const int nye = VM * HM * wte;
+    const int used = 8 * (wte + (V::kHalo ? 2 : 0));
+    const bool edge = V::kHalo && (mx0 == 0 || d.cw + 7 - 8 * mx0 < used - 1);
+    const uint64_t budget = 2000000000ull;   // 2 s per wait
+
+    if (tid == 0) {
+        // the stages were consumed before the barrier of the previous job
+        fence_proxy_async_smem();
+        for (int k = 0; k < 2 && k < njobs; ++k) {
+            int yr, cr;
+            job_rows<HM, VM, FANCY>(k, r0, yr, cr);
+            const int s = (J0 + k) & 1;
+            issue_job<HM, VM, FANCY>(tm, L, stages + s * L.stage_bytes, bar0 + 8 * s, mx0, yr, cr, d.mcus_y);
+        }
+    }
+    // colour tasks (see the split version); this thread's first task and the
+    // per-step advance
+    const int ngroups = V::kRing ? HM * wte : (HM * wte + 1) >> 1;
+    const int rows = V::kRing ? 8 : 8 * VM;
+    const int py0 = tid / ngroups, g0 = tid - py0 * ngroups;
+    const int dpy = kCtaThreads / ngroups, dg = kCtaThreads - dpy * ngroups;
+
+    for (int k = 0; k < njobs; ++k) {
+        const int j = J0 + k, s = j & 1;
+        int yrow, crow;
+        job_rows<HM, VM, FANCY>(k, r0, yrow, crow);
+        const bool do_c = crow >= 0 && crow < d.mcus_y;
+        const bool ok = mbar_wait_bounded(bar0 + 8 * s, (ps.parity >> s) & 1u, budget);
+        ps.parity ^= 1u << s;
+        if (!ok) *abort_flag = 1;
+        uint8_t *stage = stages + s * L.stage_bytes;
+        uint8_t *yplane = yplanes + s * L.ybytes;
+        uint8_t *slot = cslots + (j & (L.nslot - 1)) * L.slot_bytes;
+        const int ntask = (yrow >= 0 ? nye : 0) + (do_c ? 2 * nce : 0);
+        for (int t = tid; ok && t < ntask; t += kCtaThreads) {
+            uint32_t blk;
+            const int *q;
+            uint8_t *dst;
+            int pitch;
+            int tc = t;
+            if (yrow >= 0 && t < nye) {
+                const int vy = t / (HM * wte), bx = t - vy * (HM * wte);
+                blk = smem_u32(stage + L.stage_y + (vy * HM * wt + bx) * 128);
+                q = qs;
+                dst = yplane + 8 * vy * L.ypitch + 8 * bx;
+                pitch = L.ypitch;
+            } else {
+                if (yrow >= 0) tc -= nye;
+                const int comp = tc >= nce;
+                const int lb = lb0 + (comp ? tc - nce : tc);
+                blk = smem_u32(stage + L.stage_c + comp * L.cbytes + lb * 128);
+                q = qs + 64 * (1 + comp);
+                dst = slot + comp * 8 * L.lc + 8 * lb;
+                pitch = L.lc;
+            }
+            if (Q8)
+                idct_block_q8(blk, reinterpret_cast<const uint32_t *>(q), dst, pitch);
+            else
+                idct_block(blk, q, dst, pitch);
+        }
+        __syncthreads();
+        if (*abort_flag) {
+            if (tid == 0) {
+                atomicExch(err, kErrTimeout);
+                // the other stage may still have a copy in flight: wait for it (bounded)
+                if (k + 1 < njobs) mbar_wait_bounded(bar0 + 8 * (s ^ 1), (ps.parity >> (s ^ 1)) & 1u, budget);
+            }
+            return false;
+        }
+        if (tid == 0 && k + 2 < njobs) {
+            int yr, cr;
+            job_rows<HM, VM, FANCY>(k + 2, r0, yr, cr);
+            fence_proxy_async_smem();
+            issue_job<HM, VM, FANCY>(tm, L, stage, bar0 + 8 * s, mx0, yr, cr, d.mcus_y);
+        }
+        if (edge && do_c) {
+            fix_edges(slot, L.lc, mx0, d.cw, used, tid);
+            __syncthreads();
+        }
+        if (k >= V::kPro) {
+            const int r = r0 + k - V::kPro;
+            int py = py0, g = g0;
+            while (py < rows) {
+                if (V::kRing)
+                    cc_task_h2v2_pair(d, L, yplane, cslots, j, r, mx0, py, g);
+                else
+                    cc_task<HM, VM, FANCY>(d, L, yplane, cslots, j, r, mx0, wte, py, g);
+                py += dpy;
+                g += dg;
+                if (g >= ngroups) { g -= ngroups; ++py; }
+            }
+        }
+    }
+    ps.job = J0 + njobs;
+    ps.sync_from = ps.job;
+    return true;
+}
+
+// One work item with the roles of its variant (see run_work_split and
+// run_work_unified).  `last` = this is the CTA's final item, or the next item
+// may use the other kind of roles: the split version then drains its
+// barriers.
+template <int HM, int VM, bool FANCY, bool Q8>
+__device__ __forceinline__ bool run_work(const CUtensorMap *tm, const ItemDesc d, const ImageDesc &qsrc, int strip,
+                                         int r0, int r1, uint8_t *smem, const SmemLayout &L, PipeState &ps, int *err,
+                                         bool last, bool reload_q)
+{
+    if (Variant<HM, VM, FANCY>::kUnified)
+        return run_work_unified<HM, VM, FANCY, Q8>(tm, d, qsrc, strip, r0, r1, smem, L, ps, err, reload_q);
+    return run_work_split<HM, VM, FANCY, Q8>(tm, d, qsrc, strip, r0, r1, smem, L, ps, err, last, reload_q);
 }
 
 }  // namespace jdec
