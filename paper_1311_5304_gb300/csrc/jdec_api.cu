@@ -214,7 +214,9 @@ jdec_status launch_rows(jdec_ctx *ctx, const jdec_image *img, const Geometry &g,
     p.img.row1 = row1;
     p.err = ctx->d_err;
     const int grid = nctas;
-    cudaError_t e = launch_fused(g.hm, g.vm, g.fancy, p, grid, smem, s);
+    // unified roles pay off on full-width strips (large images)
+    const bool unified = g.fancy && g.hm == 2 && wt >= default_wt(g);
+    cudaError_t e = launch_fused(g.hm, g.vm, g.fancy, unified, p, grid, smem, s);
     if (e != cudaSuccess) return JDEC_ECUDA;
     ctx->launches++;
     return JDEC_OK;

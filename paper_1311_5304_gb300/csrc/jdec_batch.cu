@@ -165,7 +165,9 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
                 if (imgs[i].qtab[c][k] > 255) q8 = 0;
         cls_of[i] = 2 * var[i] + q8;
         UnionLayout &u = U[cls_of[i]];
-        const SmemLayout L = smem_layout(g.hm, g.vm, g.fancy, wt[i], 4);
+        // one variant per class launch: its own number of chroma slots
+        u.nslot = default_slots(g.hm, g.vm, g.fancy);
+        const SmemLayout L = smem_layout(g.hm, g.vm, g.fancy, wt[i], u.nslot);
         u.stage_bytes = std::max(u.stage_bytes, L.stage_bytes);
         u.ybytes = std::max(u.ybytes, L.ybytes);
         u.slot_bytes = std::max(u.slot_bytes, L.slot_bytes);
@@ -174,7 +176,7 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
         UnionLayout &u = U[c];
         u.off_y = kStages * u.stage_bytes;
         u.off_c = u.off_y + 2 * u.ybytes;
-        u.off_q = u.off_c + 4 * u.slot_bytes;
+        u.off_q = u.off_c + u.nslot * u.slot_bytes;
         u.off_bar = u.off_q + 3 * 64 * 4;
         u.off_flag = u.off_bar + 8 * kStages;
         u.total = u.off_flag + 16 + 1024;
@@ -274,7 +276,7 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
             if (!cached_map(b, &bi.tmap[c], imgs[i].coef[c], imgs[i].blocks_w[c], imgs[i].blocks_h[c], wt[i] + 2 * halo, 1))
                 return JDEC_ECUDA;
         fill_desc(&bi.desc, &imgs[i], g, wt[i], 1);
-        bi.desc.nslot = 4;
+        bi.desc.nslot = default_slots(g.hm, g.vm, g.fancy);
         bi.desc.nidct = 64;
         bi.variant = var[i];
     }

@@ -42,6 +42,7 @@ struct ImageDesc {
 // consecutive items of different variants can overlap in the pipeline.
 struct UnionLayout {
     int stage_bytes, off_y, ybytes, off_c, slot_bytes, off_q, off_bar, off_flag, total;
+    int nslot;   // chroma slots (4 when items of several variants share the layout)
 };
 
 // One image of a batched launch (device memory, 128-byte aligned: the tensor
@@ -112,7 +113,7 @@ __host__ __device__ inline SmemLayout apply_union(SmemLayout L, const UnionLayou
     L.off_stage = 0;
     L.off_y = U.off_y;
     L.ybytes = U.ybytes;
-    L.nslot = 4;
+    L.nslot = U.nslot;
     L.off_c = U.off_c;
     L.slot_bytes = U.slot_bytes;
     L.off_q = U.off_q;

@@ -1,6 +1,6 @@
 // jdec_kernels.cu -- __global__ entry points of the GB300 back-end.
 //
-//   jdec_fused_kernel<HM, VM, FANCY>: one image; CTA b runs share b of the
+//   jdec_fused_kernel<HM, VM, FANCY, Q8, UNI>: one image; CTA b runs share b of the
 //     image's strip-rows (see run_share).
 //
 // Variants: (HM, VM) = (1,1) 4:4:4, (2,1) 4:2:2, (2,2) 4:2:0; FANCY selects
@@ -45,7 +45,7 @@ static cudaError_t configure_kernel(K k, ConfigFlags &f)
     return e;
 }
 
-template <int HM, int VM, bool FANCY, bool Q8>
+template <int HM, int VM, bool FANCY, bool Q8, bool UNI>
 __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_fused_kernel(const __grid_constant__ DecodeParams p)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_fused_kernel(
     }
     __syncthreads();
     PipeState ps{0u, 0, 0};
-    run_share<HM, VM, FANCY, Q8>(p.tmap, p.img, blockIdx.x, smem, L, ps, p.err, true);
+    run_share<HM, VM, FANCY, Q8, UNI>(p.tmap, p.img, blockIdx.x, smem, L, ps, p.err, true);
 }
 
 // One item of a batch with its variant's code and the union layout.
@@ -68,14 +68,15 @@ template <int HM, int VM, bool FANCY, bool Q8>
 __device__ __forceinline__ bool batch_item(const BatchParams &p, const BatchImage &bi, const BatchItem &it, uint8_t *smem,
                                            PipeState &ps, bool last, bool reload)
 {
-    const SmemLayout L = apply_union(smem_layout(HM, VM, FANCY, bi.desc.wt, 4), p.U);
+    const SmemLayout L = apply_union(smem_layout(HM, VM, FANCY, bi.desc.wt, p.U.nslot), p.U);
     // wt also sizes the layout: read once
     if (reload && threadIdx.x == 0)
         for (int c = 0; c < 3; ++c) {
             tensormap_acquire(&bi.tmap[c]);
             tma_prefetch_map(&bi.tmap[c]);
         }
-    return run_work<HM, VM, FANCY, Q8>(bi.tmap, item_desc(bi.desc), bi.desc, it.strip, it.r0, it.r1, smem, L, ps, p.err,
+    // batches hold many small and narrow images: split roles
+    return run_work<HM, VM, FANCY, Q8, false>(bi.tmap, item_desc(bi.desc), bi.desc, it.strip, it.r0, it.r1, smem, L, ps, p.err,
                                        last, reload);
 }
 
@@ -100,9 +101,7 @@ __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_batch_kernel(
         const BatchImage &bi = p.imgs[it.img];
         const bool reload = it.img != cur;
         cur = it.img;
-        // items of different variants may use different warp roles: every
-        // split-role item drains its barriers
-        const bool last = true;
+        const bool last = i + 1 == i1;
         bool ok;
         const bool q8 = bi.desc.q8 != 0;
         switch (bi.variant) {
@@ -225,10 +224,10 @@ int batch_occupancy(int smem)
     return n > 0 ? n : 1;
 }
 
-template <int HM, int VM, bool FANCY, bool Q8>
+template <int HM, int VM, bool FANCY, bool Q8, bool UNI = false>
 static cudaError_t launch_variant(const DecodeParams &p, int grid, int smem, cudaStream_t s)
 {
-    auto k = jdec_fused_kernel<HM, VM, FANCY, Q8>;
+    auto k = jdec_fused_kernel<HM, VM, FANCY, Q8, UNI>;
     static ConfigFlags configured;
     cudaError_t e = configure_kernel(k, configured);
     if (e != cudaSuccess) return e;
@@ -237,24 +236,30 @@ static cudaError_t launch_variant(const DecodeParams &p, int grid, int smem, cud
 }
 
 template <bool Q8>
-static cudaError_t launch_q(int hm, int vm, bool fancy, const DecodeParams &p, int grid, int smem, cudaStream_t s)
+static cudaError_t launch_q(int hm, int vm, bool fancy, bool uni, const DecodeParams &p, int grid, int smem,
+                            cudaStream_t s)
 {
     if (hm == 1) return launch_variant<1, 1, false, Q8>(p, grid, smem, s);
-    if (vm == 1)
-        return fancy ? launch_variant<2, 1, true, Q8>(p, grid, smem, s) : launch_variant<2, 1, false, Q8>(p, grid, smem, s);
-    return fancy ? launch_variant<2, 2, true, Q8>(p, grid, smem, s) : launch_variant<2, 2, false, Q8>(p, grid, smem, s);
+    if (vm == 1) {
+        if (!fancy) return launch_variant<2, 1, false, Q8>(p, grid, smem, s);
+        return uni ? launch_variant<2, 1, true, Q8, true>(p, grid, smem, s) : launch_variant<2, 1, true, Q8>(p, grid, smem, s);
+    }
+    if (!fancy) return launch_variant<2, 2, false, Q8>(p, grid, smem, s);
+    return uni ? launch_variant<2, 2, true, Q8, true>(p, grid, smem, s) : launch_variant<2, 2, true, Q8>(p, grid, smem, s);
 }
 
-cudaError_t launch_fused(int hm, int vm, bool fancy, const DecodeParams &p, int grid, int smem, cudaStream_t s)
+cudaError_t launch_fused(int hm, int vm, bool fancy, bool unified, const DecodeParams &p, int grid, int smem,
+                         cudaStream_t s)
 {
-    return p.img.q8 ? launch_q<true>(hm, vm, fancy, p, grid, smem, s) : launch_q<false>(hm, vm, fancy, p, grid, smem, s);
+    return p.img.q8 ? launch_q<true>(hm, vm, fancy, unified, p, grid, smem, s)
+                    : launch_q<false>(hm, vm, fancy, unified, p, grid, smem, s);
 }
 
 template <int HM, int VM, bool FANCY>
 static int occupancy_variant(int smem)
 {
     int n = 0;
-    auto k = jdec_fused_kernel<HM, VM, FANCY, true>;
+    auto k = jdec_fused_kernel<HM, VM, FANCY, true, false>;
     static ConfigFlags configured;
     if (configure_kernel(k, configured) != cudaSuccess) return 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kCtaThreads, smem) != cudaSuccess) return 1;

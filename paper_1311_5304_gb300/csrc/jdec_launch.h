@@ -6,7 +6,9 @@
 
 namespace jdec {
 
-cudaError_t launch_fused(int hm, int vm, bool fancy, const DecodeParams &p, int grid, int smem, cudaStream_t s);
+// unified: every warp transforms and converts (triangular 4:2:2 / 4:2:0 only)
+cudaError_t launch_fused(int hm, int vm, bool fancy, bool unified, const DecodeParams &p, int grid, int smem,
+                         cudaStream_t s);
 int fused_occupancy(int hm, int vm, bool fancy, int smem);
 cudaError_t launch_batch(const BatchParams &p, int grid, int smem, cudaStream_t s);
 int batch_occupancy(int smem);

@@ -122,6 +122,7 @@ jdec_status decode_batch_static(const jdec_image *imgs, int n, cudaStream_t s)
     }
     U.off_y = kStages * U.stage_bytes;
     U.off_c = U.off_y + 2 * U.ybytes;
+    U.nslot = 4;   // items of every variant share the layout
     U.off_q = U.off_c + 4 * U.slot_bytes;
     U.off_bar = U.off_q + 3 * 64 * 4;
     U.off_flag = U.off_bar + 8 * kStages;

@@ -57,9 +57,10 @@ struct Variant {
     static constexpr bool kRing = FANCY && HM == 2 && VM == 2; // vertical neighbours
     static constexpr int kLA = kRing ? 1 : 0;                  // chroma lookahead rows
     static constexpr int kPro = kRing ? 2 : 0;                 // chroma-only jobs per item
-    // every warp transforms and then converts each job (triangular 4:2:2 and
-    // 4:2:0, where colour work is close to IDCT work); else split warp roles
-    static constexpr bool kUnified = FANCY && HM == 2;
+    // every warp may transform and then convert each job (triangular 4:2:2
+    // and 4:2:0, where colour work is close to IDCT work; faster on full-width
+    // strips of large images); else split warp roles
+    static constexpr bool kCanUnify = FANCY && HM == 2;
 };
 
 // Job k of an item covering MCU rows [r0, r1): its luma row (-1: none) and
@@ -523,16 +524,16 @@ __device__ bool run_work_unified(const CUtensorMap *tm, const ItemDesc d, const 
     return true;
 }
 
-// One work item with the roles of its variant (see run_work_split and
-// run_work_unified).  `last` = this is the CTA's final item, or the next item
-// may use the other kind of roles: the split version then drains its
-// barriers.
-template <int HM, int VM, bool FANCY, bool Q8>
+// One work item with unified roles (UNI, where the variant allows it) or
+// split roles (see run_work_split and run_work_unified).  `last` = this is
+// the CTA's final item, or the next item may use the other kind of roles:
+// the split version then drains its barriers.
+template <int HM, int VM, bool FANCY, bool Q8, bool UNI>
 __device__ __forceinline__ bool run_work(const CUtensorMap *tm, const ItemDesc d, const ImageDesc &qsrc, int strip,
                                          int r0, int r1, uint8_t *smem, const SmemLayout &L, PipeState &ps, int *err,
                                          bool last, bool reload_q)
 {
-    if (Variant<HM, VM, FANCY>::kUnified)
+    if (UNI && Variant<HM, VM, FANCY>::kCanUnify)
         return run_work_unified<HM, VM, FANCY, Q8>(tm, d, qsrc, strip, r0, r1, smem, L, ps, err, reload_q);
     return run_work_split<HM, VM, FANCY, Q8>(tm, d, qsrc, strip, r0, r1, smem, L, ps, err, last, reload_q);
 }
@@ -544,7 +545,7 @@ namespace jdec {
 // Runs this CTA's share of an image: the strips' MCU rows in [row0, row1),
 // concatenated strip after strip, split evenly over `nctas` CTAs; `b` is the
 // CTA's index among them.
-template <int HM, int VM, bool FANCY, bool Q8>
+template <int HM, int VM, bool FANCY, bool Q8, bool UNI>
 __device__ bool run_share(const CUtensorMap *tm, const ImageDesc &d, int b, uint8_t *smem, const SmemLayout &L,
                           PipeState &ps, int *err, bool last_image)
 {
@@ -558,7 +559,7 @@ __device__ bool run_share(const CUtensorMap *tm, const ImageDesc &d, int b, uint
         const int rr = static_cast<int>(a - s * nrows);
         const int len = static_cast<int>(min(e - a, nrows - rr));
         a += len;
-        if (!run_work<HM, VM, FANCY, Q8>(tm, id, d, s, d.row0 + rr, d.row0 + rr + len, smem, L, ps, err,
+        if (!run_work<HM, VM, FANCY, Q8, UNI>(tm, id, d, s, d.row0 + rr, d.row0 + rr + len, smem, L, ps, err,
                                          last_image && a >= e, false))
             return false;
     }
