@@ -92,13 +92,18 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
+# Sources that decide the single-image launches' DRAM traffic: the device code
+# and the host code that plans those launches (strip widths, grids).
+TRAFFIC_SOURCES = ("jdec_api.cu", "jdec_common.h", "jdec_device.cuh", "jdec_kernels.cu", "jdec_launch.h",
+                   "jdec_work.cuh")
+
+
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1311_5304_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 

@@ -114,7 +114,8 @@ void save_tune_table(jdec_ctx *ctx)
 void autotune_shape(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cudaStream_t s)
 {
     if (tuned_wt(ctx, g) > 0 || ctx->n_tune >= 64) return;
-    static const int cand[] = {4, 6, 8, 10, 12, 14, 16, 20, 24, 32};
+    // the defaults (20/21, 31/32) fill whole rounds of the IDCT threads
+    static const int cand[] = {4, 6, 8, 10, 12, 16, 20, 21, 24, 31, 32, 42};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return;
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return; }
