@@ -67,6 +67,16 @@ typedef enum {
 #define JDEC_UPSAMPLE_FANCY     0u
 #define JDEC_UPSAMPLE_REPLICATE 1u
 
+/* Testing aid for failure detection (jdec_image.flags, jdec_decode_coeffs
+ * only): the kernel arms its coefficient-load barriers but issues no loads,
+ * so every CTA's bounded wait gives up after its limit (2 s), the CTA stops
+ * without writing any pixel, and jdec_sync_status returns JDEC_ETIMEOUT.
+ * The context stays usable.  Rejected (JDEC_EINVAL) by the batched and
+ * host-buffer calls.  Environment variable JDEC_TEST_FAIL_ALLOCS=n (read by
+ * jdec_create) makes the context's next n device-buffer allocations fail
+ * with JDEC_ENOMEM, for the same purpose. */
+#define JDEC_TEST_WITHHOLD_LOADS 0x80000000u
+
 typedef struct {
     int device;               /* CUDA device ordinal                         */
     size_t hbm_budget_bytes;  /* 0 = no limit; bounds context-owned buffers  */
@@ -86,7 +96,7 @@ typedef struct {
                                      read during the call, not retained         */
     uint8_t *rgb;                 /* DEVICE pointer to the RGB output          */
     int64_t rgb_pitch;            /* bytes per output row, >= 3*width          */
-    uint32_t flags;               /* JDEC_UPSAMPLE_*                           */
+    uint32_t flags;               /* JDEC_UPSAMPLE_* (| JDEC_TEST_*)           */
 } jdec_image;
 
 /* Creates a context on opt->device (default 0).  *out receives the context. */

@@ -81,7 +81,7 @@ bool encode_plane_map(CUtensorMap *m, const int16_t *base, int bw, int bh, int b
     return r == CUDA_SUCCESS;
 }
 
-jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers)
+jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers, bool allow_test)
 {
     if (!img) return JDEC_EINVAL;
     if (img->width < 1 || img->width > 65535 || img->height < 1 || img->height > 65535) return JDEC_EINVAL;
@@ -92,7 +92,8 @@ jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers)
         return JDEC_EUNSUPPORTED;
     const int hm = img->h_samp[0], vm = img->v_samp[0];
     if (!((hm == 1 && vm == 1) || (hm == 2 && vm == 1) || (hm == 2 && vm == 2))) return JDEC_EUNSUPPORTED;
-    if (img->flags & ~JDEC_UPSAMPLE_REPLICATE) return JDEC_EINVAL;
+    if (img->flags & ~(JDEC_UPSAMPLE_REPLICATE | JDEC_TEST_WITHHOLD_LOADS)) return JDEC_EINVAL;
+    if ((img->flags & JDEC_TEST_WITHHOLD_LOADS) && !allow_test) return JDEC_EINVAL;
     g->hm = hm; g->vm = vm;
     g->fancy = (img->flags & JDEC_UPSAMPLE_REPLICATE) == 0 && hm == 2;
     g->W = img->width; g->H = img->height;
@@ -180,6 +181,7 @@ void fill_desc(ImageDesc *d, const jdec_image *img, const Geometry &g, int wt, i
     d->nslot = default_slots(g.hm, g.vm, g.fancy);
     d->nidct = 32 * default_idct_warps(g.hm, g.vm);
     d->aligned8 = ((reinterpret_cast<uintptr_t>(img->rgb) | static_cast<uintptr_t>(img->rgb_pitch)) & 7) == 0;
+    d->withhold = (img->flags & JDEC_TEST_WITHHOLD_LOADS) ? 1 : 0;
     d->q8 = 1;
     for (int c = 0; c < 3; ++c)
         for (int k = 0; k < 64; ++k) {
@@ -245,6 +247,10 @@ int occupancy_cached(jdec_ctx *ctx, int hm, int vm, bool fancy, int smem)
 jdec_status ensure_buffer(jdec_ctx *ctx, void **buf, size_t *cap, size_t need)
 {
     if (*cap >= need) return JDEC_OK;
+    if (ctx->fail_allocs > 0) {   // injected failure (testing aid); the context stays usable
+        --ctx->fail_allocs;
+        return JDEC_ENOMEM;
+    }
     const size_t others = ctx->owned_bytes - *cap;
     if (ctx->opt.hbm_budget_bytes && others + need > ctx->opt.hbm_budget_bytes) return JDEC_EBUSY;
     if (*buf) cudaFree(*buf);
@@ -301,6 +307,7 @@ jdec_status jdec_create(jdec_ctx **out, const jdec_options *opt)
         return JDEC_ENOMEM;
     }
     jdec::load_tune_table(ctx);
+    if (const char *e = getenv("JDEC_TEST_FAIL_ALLOCS")) ctx->fail_allocs = std::max(0, atoi(e));
     *out = ctx;
     return JDEC_OK;
 }
@@ -309,11 +316,12 @@ jdec_status jdec_decode_coeffs(jdec_ctx *ctx, const jdec_image *img, void *strea
 {
     if (!ctx) return JDEC_EINVAL;
     jdec::Geometry g;
-    jdec_status st = jdec::validate(img, &g, false);
+    jdec_status st = jdec::validate(img, &g, false, true);
     if (st != JDEC_OK) return st;
     jdec::DeviceGuard dg(ctx->device);
     if (!dg.ok) return JDEC_ECUDA;
-    if (ctx->opt.autotune) jdec::autotune_shape(ctx, img, g, static_cast<cudaStream_t>(stream));
+    if (ctx->opt.autotune && !(img->flags & JDEC_TEST_WITHHOLD_LOADS))
+        jdec::autotune_shape(ctx, img, g, static_cast<cudaStream_t>(stream));
     return jdec::launch_image(ctx, img, g, static_cast<cudaStream_t>(stream), 0);
 }
 

@@ -33,6 +33,7 @@ struct ImageDesc {
     int32_t row0, row1;     // MCU rows [row0, row1) covered by the launch
     int32_t nslot;          // chroma slots of the shared-memory ring (2 or 4)
     int32_t nidct;          // threads of the IDCT warp group (32, 64 or 96)
+    int32_t withhold;       // testing aid: arm the load barriers, issue no loads
     int32_t q[3][64];       // dequantisation tables, natural order
 };
 

@@ -40,6 +40,7 @@ struct jdec_ctx {
     int *d_err = nullptr;
     size_t owned_bytes = 0;
     long launches = 0;
+    int fail_allocs = 0;   // testing aid: the next n buffer allocations fail (JDEC_TEST_FAIL_ALLOCS)
     // occupancy cache
     int occ_key[32][2];
     int occ_val[32];
@@ -62,7 +63,8 @@ namespace jdec {
 
 const char *status_str(jdec_status s);
 bool encode_plane_map(CUtensorMap *m, const int16_t *base, int bw, int bh, int box_w, int box_h);
-jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers);
+// allow_test: accept the JDEC_TEST_WITHHOLD_LOADS flag (single-image launches only)
+jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers, bool allow_test = false);
 void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int *wt, int *nctas, int *smem);
 void fill_desc(ImageDesc *d, const jdec_image *img, const Geometry &g, int wt, int nctas);
 bool encode_maps(CUtensorMap maps[3], const jdec_image *img, const Geometry &g, int wt);

@@ -31,7 +31,7 @@ struct ItemDesc {
     uint8_t *rgb;
     int64_t pitch;
     int W, H, cw, ch, mcus_x, mcus_y, wt, nidct;
-    bool aligned8;
+    bool aligned8, withhold;
 };
 
 __device__ __forceinline__ ItemDesc item_desc(const ImageDesc &d)
@@ -42,6 +42,7 @@ __device__ __forceinline__ ItemDesc item_desc(const ImageDesc &d)
     t.W = d.W; t.H = d.H; t.cw = d.cw; t.ch = d.ch;
     t.mcus_x = d.mcus_x; t.mcus_y = d.mcus_y; t.wt = d.wt; t.nidct = d.nidct;
     t.aligned8 = d.aligned8 != 0;
+    t.withhold = d.withhold != 0;
     return t;
 }
 
@@ -79,15 +80,18 @@ __device__ __forceinline__ void job_rows(int k, int r0, int &yrow, int &crow)
 }
 
 // Issues the TMA loads of one job into a stage.  Called by one thread.
+// `withhold` (testing aid): arm the barrier for the bytes but issue no load,
+// so the job's bounded wait runs out.
 template <int HM, int VM, bool FANCY>
 __device__ __forceinline__ void issue_job(const CUtensorMap *tm, const SmemLayout &L, uint8_t *stage, uint32_t bar,
-                                          int mx0, int yrow, int crow, int mcus_y)
+                                          int mx0, int yrow, int crow, int mcus_y, bool withhold)
 {
     using V = Variant<HM, VM, FANCY>;
     const bool do_y = yrow >= 0;
     const bool do_c = crow >= 0 && crow < mcus_y;
     const uint32_t bytes = (do_y ? L.ny * 128 : 0) + (do_c ? 2 * L.nc * 128 : 0);
     mbar_arrive_expect_tx(bar, bytes);
+    if (withhold) return;
     if (do_y) tma_load_3d(smem_u32(stage + L.stage_y), &tm[0], bar, 0, mx0 * HM, yrow * VM);
     if (do_c) {
         tma_load_3d(smem_u32(stage + L.stage_c), &tm[1], bar, 0, mx0 - (V::kHalo ? 1 : 0), crow);
@@ -279,7 +283,8 @@ __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const Im
                 int yr, cr;
                 job_rows<HM, VM, FANCY>(k, r0, yr, cr);
                 const int s = (J0 + k) & 1;
-                issue_job<HM, VM, FANCY>(tm, L, stages + s * L.stage_bytes, bar0 + 8 * s, mx0, yr, cr, d.mcus_y);
+                issue_job<HM, VM, FANCY>(tm, L, stages + s * L.stage_bytes, bar0 + 8 * s, mx0, yr, cr, d.mcus_y,
+                                          d.withhold);
             }
         }
         for (int k = 0; k < njobs; ++k) {
@@ -335,7 +340,7 @@ __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const Im
                 int yr, cr;
                 job_rows<HM, VM, FANCY>(k + 2, r0, yr, cr);
                 fence_proxy_async_smem();
-                issue_job<HM, VM, FANCY>(tm, L, stage, bar0 + 8 * s, mx0, yr, cr, d.mcus_y);
+                issue_job<HM, VM, FANCY>(tm, L, stage, bar0 + 8 * s, mx0, yr, cr, d.mcus_y, d.withhold);
             }
             if (edge && do_c) fix_edges(slot, L.lc, mx0, d.cw, used, tid);
             named_arrive(kBarFull0 + s, kCtaThreads);
@@ -438,7 +443,8 @@ __device__ bool run_work_unified(const CUtensorMap *tm, const ItemDesc d, const 
             int yr, cr;
             job_rows<HM, VM, FANCY>(k, r0, yr, cr);
             const int s = (J0 + k) & 1;
-            issue_job<HM, VM, FANCY>(tm, L, stages + s * L.stage_bytes, bar0 + 8 * s, mx0, yr, cr, d.mcus_y);
+            issue_job<HM, VM, FANCY>(tm, L, stages + s * L.stage_bytes, bar0 + 8 * s, mx0, yr, cr, d.mcus_y,
+                                          d.withhold);
         }
     }
     // colour tasks (see the split version); this thread's first task and the
@@ -499,7 +505,7 @@ __device__ bool run_work_unified(const CUtensorMap *tm, const ItemDesc d, const 
             int yr, cr;
             job_rows<HM, VM, FANCY>(k + 2, r0, yr, cr);
             fence_proxy_async_smem();
-            issue_job<HM, VM, FANCY>(tm, L, stage, bar0 + 8 * s, mx0, yr, cr, d.mcus_y);
+            issue_job<HM, VM, FANCY>(tm, L, stage, bar0 + 8 * s, mx0, yr, cr, d.mcus_y, d.withhold);
         }
         if (edge && do_c) {
             fix_edges(slot, L.lc, mx0, d.cw, used, tid);
