@@ -108,10 +108,11 @@ JDEC_API jdec_status jdec_create(jdec_ctx **out, const jdec_options *opt);
  * launching for inconsistent descriptions (see jdec_image). */
 JDEC_API jdec_status jdec_decode_coeffs(jdec_ctx *ctx, const jdec_image *img, void *stream);
 
-/* Decodes n images (any mix of sizes and samplings) with one persistent launch
- * over a flattened MCU work list.  The launch is recorded once per work-list
- * shape as a CUDA graph and replayed with the descriptors of each call.
- * Per-image results are identical to jdec_decode_coeffs.  n <= max_batch. */
+/* Decodes n images (any mix of sizes and samplings): per variant class one
+ * persistent launch over a flattened MCU work list, the launches recorded
+ * once per work-list shape as a CUDA graph and replayed with the descriptors
+ * of each call.  Per-image results are identical to jdec_decode_coeffs.
+ * n <= max_batch. */
 JDEC_API jdec_status jdec_decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int32_t n, void *stream);
 
 /* Same as jdec_decode_coeffs, but coef[] and rgb point to HOST memory
