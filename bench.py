@@ -298,6 +298,8 @@ def run_ours(args, ws, rank, local):
         out["batch"] = bench_batched(ctx, dev, stream, args.batch_steps, 2, args.batch_images)
     if not args.no_serve:
         out["serving"] = bench_serving(ctx, dev, [2000, 5000, 10000, 20000, 50000], args.serve_requests, 8.0)
+    if not args.no_jpeg:
+        out["jpeg"] = bench_jpeg(ctx, dev, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(imgs, args.cpu_seconds)
     if ws > 1:
@@ -359,6 +361,58 @@ def bench_batched(ctx, dev, stream, steps, warmup, nimages=1024):
             "plain": {"ms": round(t_plain, 3), "mpix_s": round(px / t_plain / 1e3, 1), "launches": len(descs),
                       "api": "jdec_decode_coeffs per image"},
             "speedup_batched_vs_plain": round(t_plain / t_batch, 3)}
+
+
+def bench_jpeg(ctx, dev, stream, reps=3):
+    """Whole-stream decode of one 8192x8192 4:2:0 q90 JPEG (restart marker at
+    every MCU row) from host bytes to device RGB: host entropy decoding then
+    one back-end launch, against jdec_decode_jpeg, which overlaps chunked
+    host decoding with the back-end (1 thread) and decodes restart-aligned
+    chunks on all host cores.  Wall-clock times (host decoding is the
+    dominant stage)."""
+    import torch
+    from paper_1311_5304_gb300 import jdec, synth
+    img = synth.make_image(SIDE, SIDE, "420", QUALITY, seed=SEED, kind="texture", sigma=4.0, cover=0.85, fancy=True)
+    mx = img.planes[0].shape[1] // 2
+    data = synth.encode_jfif(img, mx)
+    ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    rgb = torch.empty((SIDE, SIDE, 3), dtype=torch.uint8, device=dev)
+    info = jdec.jpeg_parse(data)
+    hplanes = [torch.empty((info.blocks_h[c], info.blocks_w[c], 64), dtype=torch.int16).pin_memory() for c in range(3)]
+    dplanes = [torch.empty_like(p, device=dev) for p in hplanes]
+    keep = []
+    desc = jdec.make_image(SIDE, SIDE, "420", dplanes, [np.array(info.qtab[c][:], np.uint16) for c in range(3)],
+                           rgb, keep=keep)
+
+    def serial():
+        jdec.entropy_decode(data, hplanes)
+        for h, d in zip(hplanes, dplanes):
+            d.copy_(h, non_blocking=True)
+        ctx.decode_coeffs(desc, stream)
+
+    def timed(fn):
+        fn()
+        ctx.sync(stream)
+        ts = []
+        for _ in range(reps):
+            t = time.perf_counter()
+            fn()
+            ctx.sync(stream)
+            ts.append(time.perf_counter() - t)
+        return min(ts) * 1e3
+
+    t_serial = timed(serial)
+    t_pipe1 = timed(lambda: ctx.decode_jpeg(data, rgb, threads=1, stream=stream))
+    t_pipen = timed(lambda: ctx.decode_jpeg(data, rgb, threads=ncores, stream=stream))
+    mpix = SIDE * SIDE / 1e6
+    return {"workload": "8192x8192 4:2:0 q90 texture JPEG, restart interval = 1 MCU row",
+            "jpeg_mbytes": round(len(data) / 1e6, 1), "host_cores": ncores,
+            "serial": {"ms": round(t_serial, 1), "mpix_s": round(mpix / t_serial * 1e3, 1),
+                       "api": "jdec_entropy_decode (1 thread) + copy + jdec_decode_coeffs"},
+            "pipelined_1_thread": {"ms": round(t_pipe1, 1), "mpix_s": round(mpix / t_pipe1 * 1e3, 1),
+                                   "api": "jdec_decode_jpeg threads=1"},
+            "pipelined_all_cores": {"ms": round(t_pipen, 1), "mpix_s": round(mpix / t_pipen * 1e3, 1),
+                                    "api": f"jdec_decode_jpeg threads={ncores}"}}
 
 
 def bench_serving(ctx, dev, rates, max_requests, budget_gb):
@@ -463,6 +517,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-jpeg", action="store_true", help="skip the whole-stream JPEG decode timing")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--batch-steps", type=int, default=6)
     ap.add_argument("--batch-images", type=int, default=1024)

@@ -153,6 +153,26 @@ JDEC_API jdec_status jdec_jpeg_parse(const uint8_t *data, size_t size, jdec_jpeg
  * blocks_h[c] * 64 int16 as reported by jdec_jpeg_parse). */
 JDEC_API jdec_status jdec_entropy_decode(const uint8_t *data, size_t size, int16_t *const planes[3]);
 
+/* Same result with up to `threads` host threads: chunks of MCU rows that
+ * start at restart intervals are decoded independently.  A stream without
+ * restart intervals is decoded by the calling thread. */
+JDEC_API jdec_status jdec_entropy_decode_mt(const uint8_t *data, size_t size, int16_t *const planes[3],
+                                            int32_t threads);
+
+/* Decodes a baseline JPEG stream held in HOST memory into DEVICE RGB
+ * (rgb_pitch >= 3*width; flags: JDEC_UPSAMPLE_*), overlapping host entropy
+ * decoding with the device back-end (Sec. 4.5): the MCU rows are cut into
+ * chunks; each decoded chunk is copied to context-owned device planes and
+ * transformed while the host decodes the next ones.  With restart intervals
+ * that fall on chunk boundaries, chunks are entropy-decoded by up to
+ * `threads` host threads in parallel; otherwise by the calling thread in
+ * order.  Returns when host decoding is done; the device work completes in
+ * order on `stream`.  The stream bytes are not needed after the call.
+ * Malformed streams return JDEC_EINVAL (rows before the error may already be
+ * written); unsupported ones JDEC_EUNSUPPORTED. */
+JDEC_API jdec_status jdec_decode_jpeg(jdec_ctx *ctx, const uint8_t *data, size_t size, uint8_t *rgb,
+                                      int64_t rgb_pitch, uint32_t flags, int32_t threads, void *stream);
+
 /* Batched decode for callers that cannot allocate device memory (no
  * counterpart in the paper: a deployment need).  Some callers cannot call
  * cudaMalloc -- code running while a stream is captured into a CUDA graph,

@@ -11,7 +11,13 @@
 // markers reset the DC predictors.
 #include <cstdint>
 #include <cstring>
+#include <algorithm>
+#include <atomic>
 #include <new>
+#include <thread>
+#include <vector>
+
+#include "jdec_entropy.h"
 
 #include "../../include/jdec.h"
 
@@ -260,7 +266,191 @@ jdec_status parse(const uint8_t *data, size_t size, Parsed &P, bool need_tables)
     return JDEC_EINVAL;
 }
 
+// Decoder state that carries from one run of MCUs to the next.
+struct ScanState {
+    BitReader br;
+    int pred[3] = {0, 0, 0};
+    long todo = 0;   // MCUs left in the current restart interval
+};
+
+int mcus_x(const jdec_jpeg_info &in)
+{
+    int hmax = 1;
+    for (int c = 0; c < 3; ++c)
+        if (in.h_samp[c] > hmax) hmax = in.h_samp[c];
+    return (in.width + 8 * hmax - 1) / (8 * hmax);
+}
+
+int mcus_y(const jdec_jpeg_info &in)
+{
+    int vmax = 1;
+    for (int c = 0; c < 3; ++c)
+        if (in.v_samp[c] > vmax) vmax = in.v_samp[c];
+    return (in.height + 8 * vmax - 1) / (8 * vmax);
+}
+
+// Decodes MCUs [m0, m1) (raster order) into the full-size planes.
+jdec_status decode_mcus(const Parsed &P, ScanState &S, int16_t *const planes[3], long m0, long m1)
+{
+    const int *zz = zigzag();
+    const jdec_jpeg_info &in = P.info;
+    const int mx = mcus_x(in);
+    BitReader &br = S.br;
+    for (long mcu = m0; mcu < m1; ++mcu) {
+        if (in.restart_interval && S.todo == 0) {
+            // expect RSTn at the marker the reader stopped on
+            const uint8_t *q = br.p;
+            if (!br.marker) {
+                // the reader may have buffered padding bits only; skip to the marker
+                while (q + 1 < br.end && !(q[0] == 0xFF && q[1] != 0x00)) ++q;
+            }
+            if (!(q + 1 < br.end && q[0] == 0xFF && q[1] >= 0xD0 && q[1] <= 0xD7)) return JDEC_EINVAL;
+            br.reset_at(q + 2);
+            S.pred[0] = S.pred[1] = S.pred[2] = 0;
+            S.todo = in.restart_interval;
+        }
+        const int mcx = static_cast<int>(mcu % mx), mcy = static_cast<int>(mcu / mx);
+        for (int i = 0; i < 3; ++i) {
+            const int c = P.scan_order[i];
+            const HuffTable &dct = P.dc[P.td[i]], &act = P.ac[P.ta[i]];
+            for (int v = 0; v < in.v_samp[c]; ++v)
+                for (int h = 0; h < in.h_samp[c]; ++h) {
+                    const long bx = static_cast<long>(mcx) * in.h_samp[c] + h;
+                    const long by = static_cast<long>(mcy) * in.v_samp[c] + v;
+                    int16_t *blk = planes[c] + 64 * (by * in.blocks_w[c] + bx);
+                    memset(blk, 0, 64 * sizeof(int16_t));
+                    const int t = decode_symbol(br, dct);
+                    if (t < 0 || t > 11) return JDEC_EINVAL;
+                    S.pred[c] += extend(br.get(t), t);
+                    blk[0] = static_cast<int16_t>(S.pred[c]);
+                    for (int k = 1; k < 64; ++k) {
+                        const int rs = decode_symbol(br, act);
+                        if (rs < 0) return JDEC_EINVAL;
+                        const int r = rs >> 4, sz = rs & 15;
+                        if (sz == 0) {
+                            if (r == 15) {
+                                k += 15;
+                                continue;
+                            }
+                            break;
+                        }
+                        k += r;
+                        if (k > 63 || sz > 10) return JDEC_EINVAL;
+                        blk[zz[k]] = static_cast<int16_t>(extend(br.get(sz), sz));
+                    }
+                }
+        }
+        if (in.restart_interval) --S.todo;
+    }
+    return JDEC_OK;
+}
+
 }  // namespace
+
+// ---- internal interface used by the pipelined decoder (jdec_pipeline.cu) ----
+namespace jdec {
+
+struct JpegScan {
+    Parsed P;
+    const uint8_t *data = nullptr, *end = nullptr;
+    ScanState seq;                       // state of the sequential decoder
+    std::vector<const uint8_t *> rst;    // start of restart interval i (i >= 1: after RST i-1)
+    bool rst_indexed = false;
+};
+
+jdec_status scan_open(const uint8_t *data, size_t size, JpegScan **out, jdec_jpeg_info *info)
+{
+    if (!out) return JDEC_EINVAL;
+    JpegScan *J = new (std::nothrow) JpegScan();
+    if (!J) return JDEC_ENOMEM;
+    const jdec_status st = parse(data, size, J->P, true);
+    if (st != JDEC_OK) {
+        delete J;
+        return st;
+    }
+    J->data = data;
+    J->end = data + size;
+    J->seq.br.reset_at(J->P.scan);
+    J->seq.br.end = J->end;
+    J->seq.todo = J->P.info.restart_interval;
+    if (info) *info = J->P.info;
+    *out = J;
+    return JDEC_OK;
+}
+
+void scan_close(JpegScan *J) { delete J; }
+
+// Rows between chunk boundaries that fall on restart-interval starts (chunks
+// that begin there decode independently), or 0 when the stream has no
+// restart intervals.
+int scan_row_step(const JpegScan *J)
+{
+    const long ri = J->P.info.restart_interval;
+    if (ri <= 0) return 0;
+    const long mx = mcus_x(J->P.info);
+    long step = 1;
+    while ((step * mx) % ri != 0) {
+        ++step;
+        if (step > 65535) return 0;
+    }
+    return static_cast<int>(step);
+}
+
+// Finds every restart marker of the entropy-coded segment (byte-stuffed
+// 0xFF00 pairs are data; 0xFFD0..D7 start the next interval).
+static void index_restarts(JpegScan *J)
+{
+    if (J->rst_indexed) return;
+    J->rst.clear();
+    J->rst.push_back(J->P.scan);
+    const uint8_t *q = J->P.scan, *e = J->end;
+    while (q + 1 < e) {
+        q = static_cast<const uint8_t *>(memchr(q, 0xFF, static_cast<size_t>(e - q - 1)));
+        if (!q) break;
+        const uint8_t m = q[1];
+        if (m >= 0xD0 && m <= 0xD7) {
+            J->rst.push_back(q + 2);
+            q += 2;
+        } else if (m == 0x00 || m == 0xFF) {
+            q += (m == 0x00) ? 2 : 1;
+        } else {
+            break;   // EOI or another marker ends the scan
+        }
+    }
+    J->rst_indexed = true;
+}
+
+// Decodes MCU rows [r0, r1) into the full-size planes.  independent = false:
+// continue the sequential decoder (rows must follow the previous call's);
+// true: start afresh at the restart interval that begins at row r0 (r0 a
+// multiple of scan_row_step; safe to run concurrently with other
+// independent calls on disjoint rows).
+jdec_status scan_decode_rows(JpegScan *J, int16_t *const planes[3], int r0, int r1, bool independent)
+{
+    const jdec_jpeg_info &in = J->P.info;
+    const long mx = mcus_x(in);
+    if (r0 < 0 || r1 > mcus_y(in) || r0 > r1) return JDEC_EINVAL;
+    if (!independent) return decode_mcus(J->P, J->seq, planes, r0 * mx, r1 * mx);
+    const long ri = in.restart_interval;
+    if (ri <= 0 || (r0 * mx) % ri != 0) return JDEC_EINVAL;
+    const long interval = r0 * mx / ri;
+    if (interval >= static_cast<long>(J->rst.size())) return JDEC_EINVAL;
+    ScanState S;
+    S.br.reset_at(J->rst[interval]);
+    S.br.end = J->end;
+    S.todo = ri;
+    return decode_mcus(J->P, S, planes, r0 * mx, r1 * mx);
+}
+
+// Builds the restart index (call once before concurrent independent calls).
+jdec_status scan_prepare_independent(JpegScan *J)
+{
+    if (J->P.info.restart_interval <= 0) return JDEC_EINVAL;
+    index_restarts(J);
+    return JDEC_OK;
+}
+
+}  // namespace jdec
 
 extern "C" {
 
@@ -278,91 +468,48 @@ JDEC_API jdec_status jdec_jpeg_parse(const uint8_t *data, size_t size, jdec_jpeg
 JDEC_API jdec_status jdec_entropy_decode(const uint8_t *data, size_t size, int16_t *const planes[3])
 {
     if (!planes || !planes[0] || !planes[1] || !planes[2]) return JDEC_EINVAL;
-    Parsed *Pp = new (std::nothrow) Parsed();
-    if (!Pp) return JDEC_ENOMEM;
-    Parsed &P = *Pp;
-    jdec_status st = parse(data, size, P, true);
-    if (st != JDEC_OK) {
-        delete Pp;
+    jdec::JpegScan *J = nullptr;
+    jdec_jpeg_info info;
+    jdec_status st = jdec::scan_open(data, size, &J, &info);
+    if (st != JDEC_OK) return st;
+    st = jdec::scan_decode_rows(J, planes, 0, mcus_y(info), false);
+    jdec::scan_close(J);
+    return st;
+}
+
+JDEC_API jdec_status jdec_entropy_decode_mt(const uint8_t *data, size_t size, int16_t *const planes[3],
+                                            int32_t threads)
+{
+    if (!planes || !planes[0] || !planes[1] || !planes[2]) return JDEC_EINVAL;
+    jdec::JpegScan *J = nullptr;
+    jdec_jpeg_info info;
+    jdec_status st = jdec::scan_open(data, size, &J, &info);
+    if (st != JDEC_OK) return st;
+    const int my = mcus_y(info);
+    const int step = jdec::scan_row_step(J);
+    if (threads <= 1 || step <= 0 || step >= my || jdec::scan_prepare_independent(J) != JDEC_OK) {
+        st = jdec::scan_decode_rows(J, planes, 0, my, false);
+        jdec::scan_close(J);
         return st;
     }
-    const int *zz = zigzag();
-    const jdec_jpeg_info &in = P.info;
-    int hmax = 1, vmax = 1;
-    for (int c = 0; c < 3; ++c) {
-        if (in.h_samp[c] > hmax) hmax = in.h_samp[c];
-        if (in.v_samp[c] > vmax) vmax = in.v_samp[c];
-    }
-    const int mx = (in.width + 8 * hmax - 1) / (8 * hmax);
-    const int my = (in.height + 8 * vmax - 1) / (8 * vmax);
-    BitReader br;
-    br.reset_at(P.scan);
-    br.end = data + size;
-    int pred[3] = {0, 0, 0};
-    const long nmcu = static_cast<long>(mx) * my;
-    long todo = in.restart_interval;
-    for (long mcu = 0; mcu < nmcu; ++mcu) {
-        if (in.restart_interval && todo == 0) {
-            // expect RSTn at the marker the reader stopped on
-            const uint8_t *q = br.p;
-            if (!br.marker) {
-                // the reader may have buffered padding bits only; skip to the marker
-                while (q + 1 < br.end && !(q[0] == 0xFF && q[1] != 0x00)) ++q;
+    // chunks of whole restart-aligned row groups, several per thread
+    const int want = std::max(1, my / (4 * threads));
+    const int chunk = std::max(step, (want + step - 1) / step * step);
+    const int nch = (my + chunk - 1) / chunk;
+    std::atomic<int> next{0};
+    std::atomic<int> err{0};
+    std::vector<std::thread> pool;
+    for (int w = 0; w < std::min(threads, nch); ++w)
+        pool.emplace_back([&]() {
+            for (int k; (k = next.fetch_add(1)) < nch;) {
+                const int r0 = k * chunk, r1 = std::min(my, r0 + chunk);
+                const jdec_status r = jdec::scan_decode_rows(J, planes, r0, r1, true);
+                if (r != JDEC_OK) err.store(static_cast<int>(r));
             }
-            if (!(q + 1 < br.end && q[0] == 0xFF && q[1] >= 0xD0 && q[1] <= 0xD7)) {
-                st = JDEC_EINVAL;
-                break;
-            }
-            br.reset_at(q + 2);
-            pred[0] = pred[1] = pred[2] = 0;
-            todo = in.restart_interval;
-        }
-        const int mcx = static_cast<int>(mcu % mx), mcy = static_cast<int>(mcu / mx);
-        for (int i = 0; i < 3 && st == JDEC_OK; ++i) {
-            const int c = P.scan_order[i];
-            const HuffTable &dct = P.dc[P.td[i]], &act = P.ac[P.ta[i]];
-            for (int v = 0; v < in.v_samp[c]; ++v)
-                for (int h = 0; h < in.h_samp[c]; ++h) {
-                    const long bx = static_cast<long>(mcx) * in.h_samp[c] + h;
-                    const long by = static_cast<long>(mcy) * in.v_samp[c] + v;
-                    int16_t *blk = planes[c] + 64 * (by * in.blocks_w[c] + bx);
-                    memset(blk, 0, 64 * sizeof(int16_t));
-                    const int t = decode_symbol(br, dct);
-                    if (t < 0 || t > 11) {
-                        st = JDEC_EINVAL;
-                        break;
-                    }
-                    pred[c] += extend(br.get(t), t);
-                    blk[0] = static_cast<int16_t>(pred[c]);
-                    for (int k = 1; k < 64; ++k) {
-                        const int rs = decode_symbol(br, act);
-                        if (rs < 0) {
-                            st = JDEC_EINVAL;
-                            break;
-                        }
-                        const int r = rs >> 4, s = rs & 15;
-                        if (s == 0) {
-                            if (r == 15) {
-                                k += 15;
-                                continue;
-                            }
-                            break;
-                        }
-                        k += r;
-                        if (k > 63 || s > 10) {
-                            st = JDEC_EINVAL;
-                            break;
-                        }
-                        blk[zz[k]] = static_cast<int16_t>(extend(br.get(s), s));
-                    }
-                    if (st != JDEC_OK) break;
-                }
-        }
-        if (st != JDEC_OK) break;
-        if (in.restart_interval) --todo;
-    }
-    delete Pp;
-    return st;
+        });
+    for (auto &t : pool) t.join();
+    jdec::scan_close(J);
+    return static_cast<jdec_status>(err.load());
 }
 
 }  // extern "C"

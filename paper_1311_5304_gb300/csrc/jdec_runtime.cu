@@ -259,6 +259,7 @@ void release_runtime(jdec_ctx *ctx)
     for (int i = 0; i < ctx->n_band_ev; ++i) cudaEventDestroy(ctx->band_ev[i]);
     ctx->n_band_ev = 0;
     release_batch(ctx);
+    release_pipeline(ctx);
 }
 
 }  // namespace jdec

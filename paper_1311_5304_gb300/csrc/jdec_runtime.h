@@ -57,6 +57,15 @@ struct jdec_ctx {
     int n_band_ev = 0;
     // batched path
     jdec::BatchState *batch = nullptr;
+    // pipelined JPEG path: device planes, page-locked staging, streams, events
+    void *p_coef = nullptr;
+    size_t p_coef_cap = 0;
+    void *p_host = nullptr;
+    size_t p_host_cap = 0;
+    cudaStream_t p_h2d = nullptr, p_comp = nullptr;
+    cudaEvent_t p_ev[66];
+    int n_p_ev = 0;
+    bool p_pending = false;   // p_ev[65] guards the staging buffer until its copies ran
 };
 
 namespace jdec {
@@ -87,6 +96,9 @@ void autotune_shape(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cud
 jdec_status decode_host_banded(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cudaStream_t s);
 jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStream_t s);
 void release_runtime(jdec_ctx *ctx);
+jdec_status decode_jpeg(jdec_ctx *ctx, const uint8_t *data, size_t size, uint8_t *rgb, int64_t pitch, uint32_t flags,
+                        int threads, cudaStream_t s);
+void release_pipeline(jdec_ctx *ctx);
 void release_batch(jdec_ctx *ctx);
 
 }  // namespace jdec

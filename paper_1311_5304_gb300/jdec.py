@@ -98,6 +98,11 @@ def load(build_if_missing: bool = True, path: str | None = None):
         lib.jdec_jpeg_parse.restype = ctypes.c_int
         lib.jdec_entropy_decode.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p * 3)]
         lib.jdec_entropy_decode.restype = ctypes.c_int
+        lib.jdec_entropy_decode_mt.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p * 3),
+                                               ctypes.c_int32]
+        lib.jdec_entropy_decode_mt.restype = ctypes.c_int
+        lib.jdec_decode_jpeg.argtypes = [P, P, ctypes.c_size_t, P, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int32, P]
+        lib.jdec_decode_jpeg.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -109,7 +114,7 @@ def status_str(status: int) -> str:
 def exported_symbols() -> list[str]:
     return ["jdec_create", "jdec_decode_coeffs", "jdec_decode_batch", "jdec_decode_host",
             "jdec_sync_status", "jdec_destroy", "jdec_status_str", "jdec_jpeg_parse", "jdec_entropy_decode",
-            "jdec_decode_batch_static"]
+            "jdec_decode_batch_static", "jdec_decode_jpeg", "jdec_entropy_decode_mt"]
 
 
 def decode_batch_static(imgs, stream=None, check=True) -> int:
@@ -132,12 +137,16 @@ def jpeg_parse(data) -> JpegInfo:
     return info
 
 
-def entropy_decode(data, planes) -> None:
+def entropy_decode(data, planes, threads: int = 1) -> None:
     """Huffman-decodes `data` into 3 host int16 planes (numpy arrays or pinned
-    torch CPU tensors) shaped (blocks_h, blocks_w, 64).  Releases the GIL."""
+    torch CPU tensors) shaped (blocks_h, blocks_w, 64), on up to `threads`
+    host threads when the stream has restart intervals.  Releases the GIL."""
     ptrs = (ctypes.c_void_p * 3)(*[(p.ctypes.data if isinstance(p, np.ndarray) else p.data_ptr()) for p in planes])
     buf = data if isinstance(data, bytes) else bytes(data)
-    st = load().jdec_entropy_decode(ctypes.c_char_p(buf), len(buf), ctypes.byref(ptrs))
+    if threads > 1:
+        st = load().jdec_entropy_decode_mt(ctypes.c_char_p(buf), len(buf), ctypes.byref(ptrs), int(threads))
+    else:
+        st = load().jdec_entropy_decode(ctypes.c_char_p(buf), len(buf), ctypes.byref(ptrs))
     if st != OK:
         raise JdecError(st, "jdec_entropy_decode")
 
@@ -231,6 +240,18 @@ class Context:
         st = self._lib.jdec_decode_batch(self._h, arr, len(imgs), ctypes.c_void_p(_stream_ptr(stream)))
         if check and st != OK:
             raise JdecError(st, "jdec_decode_batch")
+        return st
+
+    def decode_jpeg(self, data: bytes, rgb, fancy: bool = True, threads: int = 1, stream=None,
+                    check=True) -> int:
+        """Baseline JPEG bytes (host) -> device RGB tensor (H, W, 3) or (H, pitch)
+        uint8; host entropy decoding overlaps the device back-end."""
+        buf = bytes(data)
+        st = self._lib.jdec_decode_jpeg(self._h, ctypes.c_char_p(buf), len(buf), ctypes.c_void_p(rgb.data_ptr()),
+                                        int(rgb.stride(0)), UPSAMPLE_FANCY if fancy else UPSAMPLE_REPLICATE,
+                                        int(threads), ctypes.c_void_p(_stream_ptr(stream)))
+        if check and st != OK:
+            raise JdecError(st, "jdec_decode_jpeg")
         return st
 
     def decode_host(self, img: Image, stream=None, check=True) -> int:

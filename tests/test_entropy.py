@@ -66,3 +66,35 @@ def test_large_image_throughput_sane():
     for c in range(3):
         assert np.array_equal(planes[c], img.planes[c])
     assert dt < 2.0
+
+
+def _decode_mt(data, threads):
+    info = jdec.jpeg_parse(data)
+    planes = [np.full((info.blocks_h[c], info.blocks_w[c], 64), 0x5A5A, np.int16) for c in range(3)]
+    jdec.entropy_decode(data, planes, threads=threads)
+    return planes
+
+
+@pytest.mark.parametrize("sampling", ["444", "422", "420"])
+@pytest.mark.parametrize("restart_rows", [None, 1, 3])
+def test_threaded_decode_equals_sequential(sampling, restart_rows):
+    # restart intervals of whole MCU rows (chunks start at rows), of a
+    # fraction of a row that lines up every few rows, or none (one thread)
+    img = synth.make_image(509, 389, sampling, 85, seed=31, kind="texture", sigma=4)
+    mx = img.planes[0].shape[1] // img.h_samp[0]
+    restart = 0 if restart_rows is None else (mx * restart_rows if restart_rows != 3 else 7)
+    data = synth.encode_jfif(img, restart)
+    for threads in (2, 5, 16):
+        planes = _decode_mt(data, threads)
+        for c in range(3):
+            assert np.array_equal(planes[c], img.planes[c]), (threads, c)
+
+
+def test_threaded_decode_rejects_truncated_stream():
+    img = synth.make_image(256, 256, "420", 80, seed=5, kind="texture", sigma=4)
+    mx = img.planes[0].shape[1] // 2
+    data = synth.encode_jfif(img, mx)
+    info = jdec.jpeg_parse(data)
+    planes = [np.zeros((info.blocks_h[c], info.blocks_w[c], 64), np.int16) for c in range(3)]
+    with pytest.raises(jdec.JdecError):
+        jdec.entropy_decode(data[: len(data) // 2], planes, threads=4)
