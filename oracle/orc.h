@@ -18,9 +18,11 @@
  * DCT->IDCT round trips, Alg. 2 in floating point (exhaustive over 2^24),
  * Alg. 1 as printed, upsampling invariants, and a second naive per-pixel
  * implementation on tiny images.  The particular 13-bit LLM flowgraph is the
- * one choice the pins cannot single out ("parity unpinned" for that choice
- * only): any exact factorisation with the same 12 constants gives the same
- * integers, and both sides are checked against the same bounds.
+ * one choice those pins cannot single out (any accurate factorisation passes
+ * them).  It is pinned instead by an independent decoder: NVIDIA's nvJPEG
+ * library gives exactly the oracle's RGB bytes (replicated chroma) on the
+ * encoder's streams at several qualities and all three samplings
+ * (tests/test_gpu_nvjpeg.py, which needs the GPU machine).
  */
 #ifndef ORC_H
 #define ORC_H
