@@ -98,12 +98,20 @@ TRAFFIC_SOURCES = ("jdec_api.cu", "jdec_common.h", "jdec_device.cuh", "jdec_kern
                    "jdec_work.cuh")
 
 
+def _code_only(text: str) -> str:
+    """Source text without comments and with whitespace collapsed (comment
+    edits do not change the kernels)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1311_5304_gb300", "csrc")
     for name in TRAFFIC_SOURCES:
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(csrc, name), encoding="utf-8") as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -16,7 +16,7 @@ constexpr int kStages = 2;          // coefficient double buffer
 
 // Error codes a kernel writes to the context's device error word.
 constexpr int kErrTimeout = 1;      // an mbarrier wait gave up
-constexpr int kErrBadWork = 2;      // a work item failed validation on device
+constexpr int kErrBadWork = 2;      // reserved: a work item that fails validation on device
 
 // Per-image description as the kernels see it.
 struct ImageDesc {
@@ -32,7 +32,7 @@ struct ImageDesc {
     int32_t q8;             // every quantisation step fits in 8 bits (dp2a path)
     int32_t row0, row1;     // MCU rows [row0, row1) covered by the launch
     int32_t nslot;          // chroma slots of the shared-memory ring (2 or 4)
-    int32_t nidct;          // threads of the IDCT warp group (32, 64 or 96)
+    int32_t nidct;          // IDCT threads of the split roles (32, 64 or 96; unified roles: unused)
     int32_t withhold;       // testing aid: arm the load barriers, issue no loads
     int32_t q[3][64];       // dequantisation tables, natural order
 };

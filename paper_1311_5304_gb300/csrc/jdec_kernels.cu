@@ -76,13 +76,14 @@ __device__ __forceinline__ bool batch_item(const BatchParams &p, const BatchImag
             tma_prefetch_map(&bi.tmap[c]);
         }
     // batches hold many small and narrow images: split roles
-    return run_work<HM, VM, FANCY, Q8, false>(bi.tmap, item_desc(bi.desc), bi.desc, it.strip, it.r0, it.r1, smem, L, ps, p.err,
-                                       last, reload);
+    return run_work<HM, VM, FANCY, Q8, false>(bi.tmap, item_desc(bi.desc), bi.desc, it.strip, it.r0, it.r1, smem, L, ps,
+                                              p.err, last, reload);
 }
 
-//   jdec_batch_kernel: many images of any variants; CTA b runs the items
-//     [cta_first[b], cta_first[b+1]) of a flattened (image, strip, row range)
-//     work list, pipelined across item boundaries.
+//   jdec_batch_kernel: many images of any variants in one launch (used by the
+//     allocation-free entry point, whose static scratch holds one work list);
+//     CTA b runs the items [cta_first[b], cta_first[b+1]) of a flattened
+//     (image, strip, row range) work list, pipelined across item boundaries.
 __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_batch_kernel(const __grid_constant__ BatchParams p)
 {
     extern __shared__ uint8_t smem_raw[];
