@@ -80,6 +80,9 @@ def lib():
                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_int64]
             _lib.orc_backend_decode.argtypes = [ctypes.POINTER(OrcImage), P, ctypes.c_int64]
             _lib.orc_backend_decode.restype = ctypes.c_int
+            _lib.orc_backend_decode_gray.argtypes = [ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32, ctypes.c_int32,
+                                                     P, P, ctypes.c_int64]
+            _lib.orc_backend_decode_gray.restype = ctypes.c_int
             _lib.orc_backend_decode_mt.argtypes = [ctypes.POINTER(OrcImage), P, ctypes.c_int64, ctypes.c_int]
             _lib.orc_backend_decode_mt.restype = ctypes.c_int
             _lib.orc_jpeg_decode_coefs.argtypes = [P, ctypes.c_int64, ctypes.POINTER(OrcJpegInfo),
@@ -173,6 +176,19 @@ def backend_decode(width, height, h_samp, v_samp, planes, qtabs, fancy, threads:
         rc = 0 if rc > 0 else rc
     if rc != 0:
         raise ValueError("oracle: inconsistent image description")
+    return out
+
+
+def backend_decode_gray(width, height, plane, qtab) -> np.ndarray:
+    """Single-component image: plane (blocks_h, blocks_w, 64) int16; returns
+    (H, W, 3) uint8 with R = G = B = Y."""
+    p = np.ascontiguousarray(plane, np.int16)
+    q = np.ascontiguousarray(qtab, np.uint16).reshape(64)
+    out = np.zeros((height, width, 3), np.uint8)
+    rc = lib().orc_backend_decode_gray(int(width), int(height), _ptr(p), int(p.shape[1]), int(p.shape[0]), _ptr(q),
+                                       _ptr(out), 3 * width)
+    if rc != 0:
+        raise ValueError("oracle: inconsistent grayscale description")
     return out
 
 

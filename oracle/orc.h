@@ -82,6 +82,14 @@ typedef struct {
  * W x H pixels.  Returns 0, or -1 if the description is inconsistent. */
 int orc_backend_decode(const orc_image *img, uint8_t *rgb, int64_t rgb_pitch);
 
+/* Single-component (grayscale) image: one plane of blocks_w x blocks_h blocks
+ * with blocks_w = ceil(W/8), blocks_h = ceil(H/8) (a one-component frame has
+ * 8x8 MCUs, T.81 A.2.2), one table.  Each sample Y is written as the RGB
+ * triple (Y, Y, Y): the output format is interleaved RGB (Sec. 4.3), and
+ * Alg. 2 maps (Y, 128, 128) to (Y, Y, Y).  Returns 0, or -1 if inconsistent. */
+int orc_backend_decode_gray(int32_t width, int32_t height, const int16_t *coef, int32_t blocks_w,
+                            int32_t blocks_h, const uint16_t q[64], uint8_t *rgb, int64_t rgb_pitch);
+
 /* Number of threads used by orc_backend_decode_mt (images are split into
  * bands of output rows; the arithmetic is orc_backend_decode's). */
 int orc_backend_decode_mt(const orc_image *img, uint8_t *rgb, int64_t rgb_pitch,

@@ -114,6 +114,29 @@ int orc_backend_decode(const orc_image *img, uint8_t *rgb, int64_t rgb_pitch)
     return 0;
 }
 
+int orc_backend_decode_gray(int32_t width, int32_t height, const int16_t *coef, int32_t blocks_w,
+                            int32_t blocks_h, const uint16_t q[64], uint8_t *rgb, int64_t rgb_pitch)
+{
+    if (width < 1 || height < 1 || !coef || !q || !rgb || rgb_pitch < 3 * (int64_t)width) return -1;
+    if (blocks_w != (width + 7) / 8 || blocks_h != (height + 7) / 8) return -1;
+    uint8_t blk[64];
+    for (int by = 0; by < blocks_h; by++)
+        for (int bx = 0; bx < blocks_w; bx++) {
+            orc_idct_block(coef + 64 * ((int64_t)by * blocks_w + bx), q, blk);
+            for (int y = 0; y < 8; y++) {
+                const int py = by * 8 + y;
+                if (py >= height) break;
+                for (int x = 0; x < 8; x++) {
+                    const int px = bx * 8 + x;
+                    if (px >= width) break;
+                    uint8_t *o = rgb + (int64_t)py * rgb_pitch + 3 * px;
+                    o[0] = o[1] = o[2] = blk[8 * y + x];
+                }
+            }
+        }
+    return 0;
+}
+
 /* ---- threaded driver: same stages, split into contiguous ranges ---------- */
 typedef struct { job *J; int t, n, phase; } targ;
 

@@ -94,3 +94,34 @@ def test_synthetic_image_decodes_near_source(orc):
     src = np.clip(np.rint(synth.render_rgb(64, 48, img.meta["seed"], "gradient", 0.0)), 0, 255)
     psnr = 10 * np.log10(255 ** 2 / np.mean((rgb - src) ** 2))
     assert psnr > 35
+
+
+# ---- single-component (grayscale) images ------------------------------------
+
+@pytest.mark.parametrize("w,h", [(1, 1), (8, 8), (15, 17), (33, 31), (640, 481)])
+def test_gray_equals_444_with_neutral_chroma(orc, w, h):
+    # Alg. 2 maps (Y, 128, 128) to (Y, Y, Y) (grey axis, pinned exhaustively
+    # in the colour tests) and an all-zero block decodes to 128 (DC-only
+    # closed form), so a grayscale image must decode like a 4:4:4 image with
+    # all-zero chroma planes, whatever their tables.
+    rng = np.random.default_rng(w * 1000 + h)
+    img = synth.random_image(rng, w, h, "444")
+    got = orc.backend_decode_gray(w, h, img.planes[0], img.qtabs[0])
+    zero = np.zeros_like(img.planes[1])
+    want = orc.backend_decode(w, h, img.h_samp, img.v_samp, [img.planes[0], zero, zero],
+                              [img.qtabs[0], img.qtabs[1], img.qtabs[2]], True)
+    assert np.array_equal(got, want)
+
+
+def test_gray_is_the_idct_of_each_block(orc):
+    # naive per-pixel statement: pixel (x, y) = IDCT of block (x/8, y/8) at
+    # (x%8, y%8), in all three channels
+    rng = np.random.default_rng(5)
+    w, h = 37, 29
+    img = synth.random_image(rng, w, h, "444")
+    plane, q = img.planes[0], img.qtabs[0]
+    blocks = orc.idct_blocks(plane.reshape(-1, 64), q).reshape(plane.shape[0], plane.shape[1], 8, 8)
+    got = orc.backend_decode_gray(w, h, plane, q)
+    for y in range(h):
+        for x in range(w):
+            assert got[y, x].tolist() == [int(blocks[y // 8, x // 8, y % 8, x % 8])] * 3
