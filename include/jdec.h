@@ -87,7 +87,10 @@ typedef struct {
 
 typedef struct {
     int32_t width, height;        /* pixels, 1..65535                          */
-    int32_t ncomp;                /* must be 3 (Y, Cb, Cr)                     */
+    int32_t ncomp;                /* 3 (Y, Cb, Cr), or 1: grayscale -- coef[0],
+                                     qtab[0] only, h_samp[0] = v_samp[0] = 1,
+                                     blocks = ceil(W/8) x ceil(H/8), output
+                                     R = G = B = Y                             */
     uint8_t h_samp[3], v_samp[3]; /* luma (1,1) | (2,1) | (2,2); chroma (1,1)  */
     const int16_t *coef[3];       /* DEVICE pointers, 16-byte aligned, planes
                                      as described above                         */

@@ -81,11 +81,55 @@ bool encode_plane_map(CUtensorMap *m, const int16_t *base, int bw, int bh, int b
     return r == CUDA_SUCCESS;
 }
 
+// A grayscale image is decoded by the 4:4:4 kernel whose chroma tiles come
+// from this plane's single row of zero blocks: TMA fills every tile outside it
+// with zeros too, an all-zero block transforms to 128, and Alg. 2 maps
+// (Y, 128, 128) to (Y, Y, Y), so the output is exactly the grey axis.
+static __device__ __align__(256) int16_t g_zero_plane[kZeroPlaneBlocks * 64];
+
+const int16_t *zero_plane()
+{
+    static const int16_t *addr[64];
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_zero_plane) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        addr[dev] = static_cast<const int16_t *>(p);
+    }
+    return addr[dev];
+}
+
 jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers, bool allow_test)
 {
     if (!img) return JDEC_EINVAL;
     if (img->width < 1 || img->width > 65535 || img->height < 1 || img->height > 65535) return JDEC_EINVAL;
-    if (img->ncomp != 3) return img->ncomp == 1 ? JDEC_EUNSUPPORTED : JDEC_EINVAL;
+    if (img->ncomp == 1) {
+        // one component: 8x8 MCUs (T.81 A.2.2), output R = G = B = Y
+        if (img->h_samp[0] != 1 || img->v_samp[0] != 1) return JDEC_EUNSUPPORTED;
+        if (img->flags & ~(JDEC_UPSAMPLE_REPLICATE | JDEC_TEST_WITHHOLD_LOADS)) return JDEC_EINVAL;
+        if ((img->flags & JDEC_TEST_WITHHOLD_LOADS) && !allow_test) return JDEC_EINVAL;
+        g->hm = g->vm = 1;
+        g->fancy = false;
+        g->gray = true;
+        g->W = img->width; g->H = img->height;
+        g->mcus_x = (img->width + 7) / 8;
+        g->mcus_y = (img->height + 7) / 8;
+        g->cw = img->width;
+        g->ch = img->height;
+        if (img->blocks_w[0] != g->mcus_x || img->blocks_h[0] != g->mcus_y) return JDEC_EINVAL;
+        if (!img->coef[0] || !img->qtab[0]) return JDEC_EINVAL;
+        if (!host_buffers && (reinterpret_cast<uintptr_t>(img->coef[0]) & 15)) return JDEC_EINVAL;
+        if (!img->rgb || img->rgb_pitch < 3 * static_cast<int64_t>(img->width)) return JDEC_EINVAL;
+        g->coef_bytes = static_cast<int64_t>(img->blocks_w[0]) * img->blocks_h[0] * 128;
+        g->rgb_bytes = 3 * static_cast<int64_t>(img->width) * img->height;
+        return JDEC_OK;
+    }
+    if (img->ncomp != 3) return JDEC_EINVAL;
+    g->gray = false;
     for (int c = 0; c < 3; ++c)
         if (img->h_samp[c] < 1 || img->h_samp[c] > 4 || img->v_samp[c] < 1 || img->v_samp[c] > 4) return JDEC_EINVAL;
     if (img->h_samp[1] != 1 || img->v_samp[1] != 1 || img->h_samp[2] != 1 || img->v_samp[2] != 1)
@@ -183,17 +227,25 @@ void fill_desc(ImageDesc *d, const jdec_image *img, const Geometry &g, int wt, i
     d->aligned8 = ((reinterpret_cast<uintptr_t>(img->rgb) | static_cast<uintptr_t>(img->rgb_pitch)) & 7) == 0;
     d->withhold = (img->flags & JDEC_TEST_WITHHOLD_LOADS) ? 1 : 0;
     d->q8 = 1;
-    for (int c = 0; c < 3; ++c)
+    for (int c = 0; c < 3; ++c) {
+        const uint16_t *q = img->qtab[g.gray ? 0 : c];   // grayscale: the chroma blocks are zero
         for (int k = 0; k < 64; ++k) {
-            d->q[c][k] = img->qtab[c][k];
-            if (img->qtab[c][k] > 255) d->q8 = 0;
+            d->q[c][k] = q[k];
+            if (q[k] > 255) d->q8 = 0;
         }
+    }
 }
 
 bool encode_maps(CUtensorMap maps[3], const jdec_image *img, const Geometry &g, int wt)
 {
     const int halo = g.fancy ? 1 : 0;
     if (!encode_plane_map(&maps[0], img->coef[0], img->blocks_w[0], img->blocks_h[0], g.hm * wt, g.vm)) return false;
+    if (g.gray) {
+        const int16_t *z = zero_plane();
+        if (!z) return false;
+        return encode_plane_map(&maps[1], z, kZeroPlaneBlocks, 1, wt, 1) &&
+               encode_plane_map(&maps[2], z, kZeroPlaneBlocks, 1, wt, 1);
+    }
     for (int c = 1; c < 3; ++c)
         if (!encode_plane_map(&maps[c], img->coef[c], img->blocks_w[c], img->blocks_h[c], wt + 2 * halo, 1))
             return false;

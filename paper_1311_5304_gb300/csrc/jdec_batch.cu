@@ -93,6 +93,7 @@ static size_t pow2_at_least(size_t x, size_t lo)
 
 static bool cached_map(BatchState *b, CUtensorMap *out, const int16_t *base, int bw, int bh, int box_w, int box_h)
 {
+    if (!base) return false;
     const MapKey key{base, bw, bh, box_w, box_h};
     auto it = b->maps.find(key);
     if (it != b->maps.end()) {
@@ -160,7 +161,7 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
         wt[i] = std::max(1, std::min(w > 0 ? w : equal_strips(g.mcus_x, default_wt(g)), kMaxWT));
         var[i] = variant_of(g);
         int q8 = 1;
-        for (int c = 0; c < 3; ++c)
+        for (int c = 0; c < (g.gray ? 1 : 3); ++c)
             for (int k = 0; k < 64; ++k)
                 if (imgs[i].qtab[c][k] > 255) q8 = 0;
         cls_of[i] = 2 * var[i] + q8;
@@ -272,9 +273,13 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
         const int halo = g.fancy ? 1 : 0;
         if (!cached_map(b, &bi.tmap[0], imgs[i].coef[0], imgs[i].blocks_w[0], imgs[i].blocks_h[0], g.hm * wt[i], g.vm))
             return JDEC_ECUDA;
-        for (int c = 1; c < 3; ++c)
-            if (!cached_map(b, &bi.tmap[c], imgs[i].coef[c], imgs[i].blocks_w[c], imgs[i].blocks_h[c], wt[i] + 2 * halo, 1))
-                return JDEC_ECUDA;
+        for (int c = 1; c < 3; ++c) {
+            // grayscale: zero chroma tiles (see zero_plane)
+            const bool ok = g.gray ? cached_map(b, &bi.tmap[c], zero_plane(), kZeroPlaneBlocks, 1, wt[i], 1)
+                                   : cached_map(b, &bi.tmap[c], imgs[i].coef[c], imgs[i].blocks_w[c],
+                                                imgs[i].blocks_h[c], wt[i] + 2 * halo, 1);
+            if (!ok) return JDEC_ECUDA;
+        }
         fill_desc(&bi.desc, &imgs[i], g, wt[i], 1);
         bi.desc.nslot = default_slots(g.hm, g.vm, g.fancy);
         bi.desc.nidct = 64;

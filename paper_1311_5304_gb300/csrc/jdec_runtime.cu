@@ -175,8 +175,9 @@ static cudaEvent_t band_event(jdec_ctx *ctx, int i)
 jdec_status decode_host_banded(jdec_ctx *ctx, const jdec_image *himg, const Geometry &g, cudaStream_t s)
 {
     // device staging: three planes (256-byte aligned) + dense RGB
-    size_t off[3], tot = 0;
-    for (int c = 0; c < 3; ++c) {
+    const int ncomp = g.gray ? 1 : 3;
+    size_t off[3] = {0, 0, 0}, tot = 0;
+    for (int c = 0; c < ncomp; ++c) {
         off[c] = tot;
         tot += (static_cast<size_t>(himg->blocks_w[c]) * himg->blocks_h[c] * 128 + 255) & ~static_cast<size_t>(255);
     }
@@ -187,7 +188,8 @@ jdec_status decode_host_banded(jdec_ctx *ctx, const jdec_image *himg, const Geom
     if (st != JDEC_OK) return st;
 
     jdec_image dimg = *himg;
-    for (int c = 0; c < 3; ++c) dimg.coef[c] = reinterpret_cast<const int16_t *>(static_cast<uint8_t *>(ctx->h_coef) + off[c]);
+    for (int c = 0; c < ncomp; ++c)
+        dimg.coef[c] = reinterpret_cast<const int16_t *>(static_cast<uint8_t *>(ctx->h_coef) + off[c]);
     dimg.rgb = static_cast<uint8_t *>(ctx->h_rgb);
     dimg.rgb_pitch = static_cast<int64_t>(rgb_pitch);
 
@@ -205,7 +207,7 @@ jdec_status decode_host_banded(jdec_ctx *ctx, const jdec_image *himg, const Geom
     for (int k = 0; k < nb; ++k) {
         const int r0 = static_cast<int>(static_cast<long>(g.mcus_y) * k / nb);
         const int r1 = static_cast<int>(static_cast<long>(g.mcus_y) * (k + 1) / nb);
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < ncomp; ++c) {
             const int v = c ? 1 : g.vm;
             const size_t row_bytes = static_cast<size_t>(himg->blocks_w[c]) * 128;
             const size_t o = static_cast<size_t>(r0) * v * row_bytes;

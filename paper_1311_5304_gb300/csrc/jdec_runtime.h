@@ -15,6 +15,7 @@ namespace jdec {
 struct Geometry {
     int hm, vm;
     bool fancy;
+    bool gray;       // one component: decoded as 4:4:4 with all-zero chroma blocks
     int W, H;
     int mcus_x, mcus_y;
     int cw, ch;
@@ -77,6 +78,10 @@ jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers, bool
 void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int *wt, int *nctas, int *smem);
 void fill_desc(ImageDesc *d, const jdec_image *img, const Geometry &g, int wt, int nctas);
 bool encode_maps(CUtensorMap maps[3], const jdec_image *img, const Geometry &g, int wt);
+// Device address (current device) of a small all-zero coefficient plane that
+// stands in for the chroma planes of a grayscale image (null on failure).
+const int16_t *zero_plane();
+constexpr int kZeroPlaneBlocks = kMaxWT + 2;   // blocks per row of that plane (one row)
 jdec_status launch_rows(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cudaStream_t s, int row0,
                         int row1, int force_wt);
 jdec_status launch_image(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cudaStream_t s, int force_wt);

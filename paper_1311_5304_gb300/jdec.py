@@ -163,14 +163,17 @@ def _stream_ptr(stream) -> int:
 def make_image(width, height, sampling, planes, qtabs, rgb, rgb_pitch=None, fancy=True,
                keep=None, host=False) -> Image:
     """Fills a ``jdec_image``.  planes: 3 int16 arrays/tensors shaped
-    (blocks_h, blocks_w, 64); qtabs: 3 host uint16 arrays of 64; rgb: uint8
-    buffer (device tensor, or host numpy array with ``host=True``)."""
-    hs, vs = SAMPLINGS[sampling] if isinstance(sampling, str) else sampling
+    (blocks_h, blocks_w, 64), or 1 for a grayscale image (sampling "gray");
+    qtabs: one host uint16 array of 64 per plane; rgb: uint8 buffer (device
+    tensor, or host numpy array with ``host=True``)."""
+    ncomp = len(planes)
+    hs, vs = ((1, 1, 1), (1, 1, 1)) if ncomp == 1 else (SAMPLINGS[sampling] if isinstance(sampling, str) else sampling)
     im = Image()
-    im.width, im.height, im.ncomp = int(width), int(height), 3
+    im.width, im.height, im.ncomp = int(width), int(height), ncomp
     keep = keep if keep is not None else []
     for c in range(3):
         im.h_samp[c], im.v_samp[c] = int(hs[c]), int(vs[c])
+    for c in range(ncomp):
         p = planes[c]
         if host:
             p = np.ascontiguousarray(p, np.int16)
