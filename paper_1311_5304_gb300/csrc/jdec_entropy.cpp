@@ -213,15 +213,22 @@ jdec_status parse(const uint8_t *data, size_t size, Parsed &P, bool need_tables)
             P.info.height = u16be(s + 1);
             P.info.width = u16be(s + 3);
             P.info.ncomp = s[5];
-            if (P.info.ncomp != 3) return JDEC_EUNSUPPORTED;
-            if (len < 8 + 9) return JDEC_EINVAL;
-            for (int c = 0; c < 3; ++c) {
+            const int nc = P.info.ncomp;
+            if (nc != 3 && nc != 1) return JDEC_EUNSUPPORTED;
+            if (len < 8 + 3 * nc) return JDEC_EINVAL;
+            for (int c = 0; c < nc; ++c) {
                 P.comp_id[c] = s[6 + 3 * c];
                 P.info.h_samp[c] = static_cast<uint8_t>(s[7 + 3 * c] >> 4);
                 P.info.v_samp[c] = static_cast<uint8_t>(s[7 + 3 * c] & 15);
                 P.comp_q[c] = s[8 + 3 * c] & 3;
-                if (P.info.h_samp[c] < 1 || P.info.h_samp[c] > 2 || P.info.v_samp[c] < 1 || P.info.v_samp[c] > 2)
-                    return JDEC_EUNSUPPORTED;
+                if (P.info.h_samp[c] < 1 || P.info.h_samp[c] > 4 || P.info.v_samp[c] < 1 || P.info.v_samp[c] > 4)
+                    return JDEC_EINVAL;
+                if (nc == 3 && (P.info.h_samp[c] > 2 || P.info.v_samp[c] > 2)) return JDEC_EUNSUPPORTED;
+            }
+            if (nc == 1) {
+                // one component: 8x8 MCUs whatever its sampling factors (T.81 A.2.2)
+                P.info.h_samp[0] = P.info.v_samp[0] = 1;
+                for (int c = 1; c < 3; ++c) P.info.h_samp[c] = P.info.v_samp[c] = 0;
             }
             if (P.info.width < 1 || P.info.height < 1) return JDEC_EINVAL;
             have_sof = true;
@@ -232,11 +239,12 @@ jdec_status parse(const uint8_t *data, size_t size, Parsed &P, bool need_tables)
             P.info.restart_interval = u16be(s);
         } else if (m == 0xDA) {
             if (!have_sof) return JDEC_EINVAL;
-            if (s[0] != 3 || len < 6 + 2 * 3) return JDEC_EUNSUPPORTED;
-            for (int i = 0; i < 3; ++i) {
+            const int nc = P.info.ncomp;
+            if (s[0] != nc || len < 6 + 2 * nc) return JDEC_EUNSUPPORTED;
+            for (int i = 0; i < nc; ++i) {
                 const int id = s[1 + 2 * i];
                 P.scan_order[i] = -1;
-                for (int c = 0; c < 3; ++c)
+                for (int c = 0; c < nc; ++c)
                     if (P.comp_id[c] == id) P.scan_order[i] = c;
                 if (P.scan_order[i] < 0) return JDEC_EINVAL;
                 P.td[i] = s[2 + 2 * i] >> 4;
@@ -244,13 +252,13 @@ jdec_status parse(const uint8_t *data, size_t size, Parsed &P, bool need_tables)
                 if (P.td[i] > 3 || P.ta[i] > 3 || !P.dc[P.td[i]].present || !P.ac[P.ta[i]].present) return JDEC_EINVAL;
             }
             int hmax = 1, vmax = 1;
-            for (int c = 0; c < 3; ++c) {
+            for (int c = 0; c < nc; ++c) {
                 if (P.info.h_samp[c] > hmax) hmax = P.info.h_samp[c];
                 if (P.info.v_samp[c] > vmax) vmax = P.info.v_samp[c];
             }
             const int mx = (P.info.width + 8 * hmax - 1) / (8 * hmax);
             const int my = (P.info.height + 8 * vmax - 1) / (8 * vmax);
-            for (int c = 0; c < 3; ++c) {
+            for (int c = 0; c < nc; ++c) {
                 P.info.blocks_w[c] = mx * P.info.h_samp[c];
                 P.info.blocks_h[c] = my * P.info.v_samp[c];
                 if (!qt_present[P.comp_q[c]]) return JDEC_EINVAL;
@@ -310,7 +318,7 @@ jdec_status decode_mcus(const Parsed &P, ScanState &S, int16_t *const planes[3],
             S.todo = in.restart_interval;
         }
         const int mcx = static_cast<int>(mcu % mx), mcy = static_cast<int>(mcu / mx);
-        for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i < in.ncomp; ++i) {
             const int c = P.scan_order[i];
             const HuffTable &dct = P.dc[P.td[i]], &act = P.ac[P.ta[i]];
             for (int v = 0; v < in.v_samp[c]; ++v)
@@ -430,6 +438,8 @@ jdec_status scan_decode_rows(JpegScan *J, int16_t *const planes[3], int r0, int 
     const jdec_jpeg_info &in = J->P.info;
     const long mx = mcus_x(in);
     if (r0 < 0 || r1 > mcus_y(in) || r0 > r1) return JDEC_EINVAL;
+    for (int c = 0; c < in.ncomp; ++c)
+        if (!planes[c]) return JDEC_EINVAL;
     if (!independent) return decode_mcus(J->P, J->seq, planes, r0 * mx, r1 * mx);
     const long ri = in.restart_interval;
     if (ri <= 0 || (r0 * mx) % ri != 0) return JDEC_EINVAL;
@@ -467,7 +477,7 @@ JDEC_API jdec_status jdec_jpeg_parse(const uint8_t *data, size_t size, jdec_jpeg
 
 JDEC_API jdec_status jdec_entropy_decode(const uint8_t *data, size_t size, int16_t *const planes[3])
 {
-    if (!planes || !planes[0] || !planes[1] || !planes[2]) return JDEC_EINVAL;
+    if (!planes || !planes[0]) return JDEC_EINVAL;
     jdec::JpegScan *J = nullptr;
     jdec_jpeg_info info;
     jdec_status st = jdec::scan_open(data, size, &J, &info);
@@ -480,7 +490,7 @@ JDEC_API jdec_status jdec_entropy_decode(const uint8_t *data, size_t size, int16
 JDEC_API jdec_status jdec_entropy_decode_mt(const uint8_t *data, size_t size, int16_t *const planes[3],
                                             int32_t threads)
 {
-    if (!planes || !planes[0] || !planes[1] || !planes[2]) return JDEC_EINVAL;
+    if (!planes || !planes[0]) return JDEC_EINVAL;
     jdec::JpegScan *J = nullptr;
     jdec_jpeg_info info;
     jdec_status st = jdec::scan_open(data, size, &J, &info);

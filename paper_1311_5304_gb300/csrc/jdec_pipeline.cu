@@ -76,8 +76,9 @@ jdec_status decode_jpeg(jdec_ctx *ctx, const uint8_t *data, size_t size, uint8_t
     } closer{J};
 
     // the image as the back-end sees it (device planes owned by the context)
-    size_t off[3], tot = 0;
-    for (int c = 0; c < 3; ++c) {
+    const int ncomp = in.ncomp;   // 3, or 1 (grayscale)
+    size_t off[3] = {0, 0, 0}, tot = 0;
+    for (int c = 0; c < ncomp; ++c) {
         off[c] = tot;
         tot += (static_cast<size_t>(in.blocks_w[c]) * in.blocks_h[c] * 128 + 255) & ~static_cast<size_t>(255);
     }
@@ -93,10 +94,12 @@ jdec_status decode_jpeg(jdec_ctx *ctx, const uint8_t *data, size_t size, uint8_t
     memset(&dimg, 0, sizeof(dimg));
     dimg.width = in.width;
     dimg.height = in.height;
-    dimg.ncomp = 3;
+    dimg.ncomp = ncomp;
     for (int c = 0; c < 3; ++c) {
         dimg.h_samp[c] = in.h_samp[c];
         dimg.v_samp[c] = in.v_samp[c];
+    }
+    for (int c = 0; c < ncomp; ++c) {
         dimg.coef[c] = reinterpret_cast<const int16_t *>(static_cast<uint8_t *>(ctx->p_coef) + off[c]);
         dimg.blocks_w[c] = in.blocks_w[c];
         dimg.blocks_h[c] = in.blocks_h[c];
@@ -108,8 +111,9 @@ jdec_status decode_jpeg(jdec_ctx *ctx, const uint8_t *data, size_t size, uint8_t
     Geometry g;
     st = validate(&dimg, &g, false);
     if (st != JDEC_OK) return st;
-    int16_t *hplanes[3];
-    for (int c = 0; c < 3; ++c) hplanes[c] = reinterpret_cast<int16_t *>(static_cast<uint8_t *>(ctx->p_host) + off[c]);
+    int16_t *hplanes[3] = {nullptr, nullptr, nullptr};
+    for (int c = 0; c < ncomp; ++c)
+        hplanes[c] = reinterpret_cast<int16_t *>(static_cast<uint8_t *>(ctx->p_host) + off[c]);
 
     // chunk boundaries (about 8 chunks per worker when decoding in parallel)
     const int my = g.mcus_y;
@@ -171,7 +175,7 @@ jdec_status decode_jpeg(jdec_ctx *ctx, const uint8_t *data, size_t size, uint8_t
             st = scan_decode_rows(J, hplanes, b[k], b[k + 1], false);
         }
         if (st != JDEC_OK) break;
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < ncomp; ++c) {
             const int v = c ? 1 : g.vm;
             const size_t row_bytes = static_cast<size_t>(in.blocks_w[c]) * 128;
             const size_t o = static_cast<size_t>(b[k]) * v * row_bytes;

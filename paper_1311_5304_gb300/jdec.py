@@ -138,9 +138,10 @@ def jpeg_parse(data) -> JpegInfo:
 
 
 def entropy_decode(data, planes, threads: int = 1) -> None:
-    """Huffman-decodes `data` into 3 host int16 planes (numpy arrays or pinned
-    torch CPU tensors) shaped (blocks_h, blocks_w, 64), on up to `threads`
-    host threads when the stream has restart intervals.  Releases the GIL."""
+    """Huffman-decodes `data` into host int16 planes (numpy arrays or pinned
+    torch CPU tensors) shaped (blocks_h, blocks_w, 64) -- 3, or 1 for a
+    grayscale stream -- on up to `threads` host threads when the stream has
+    restart intervals.  Releases the GIL."""
     ptrs = (ctypes.c_void_p * 3)(*[(p.ctypes.data if isinstance(p, np.ndarray) else p.data_ptr()) for p in planes])
     buf = data if isinstance(data, bytes) else bytes(data)
     if threads > 1:

@@ -98,10 +98,10 @@ class Server:
             return req
         info = jdec.jpeg_parse(req.data)
         req.width, req.height = info.width, info.height
-        req.sampling = (tuple(info.h_samp), tuple(info.v_samp))
-        req.qtabs = [np.array(info.qtab[c][:], np.uint16) for c in range(3)]
+        req.sampling = (tuple(info.h_samp), tuple(info.v_samp)) if info.ncomp == 3 else "gray"
+        req.qtabs = [np.array(info.qtab[c][:], np.uint16) for c in range(info.ncomp)]
         planes = [torch.empty((info.blocks_h[c], info.blocks_w[c], 64), dtype=torch.int16, pin_memory=True)
-                  for c in range(3)]
+                  for c in range(info.ncomp)]
         jdec.entropy_decode(req.data, planes)
         req.host_planes = planes
         return req

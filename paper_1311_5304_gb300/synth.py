@@ -189,6 +189,9 @@ def _enc():
             P = _ct.c_void_p
             _syn.synth_jfif_encode.argtypes = [_ct.c_int, _ct.c_int, P, P, P, P, P, P, _ct.c_int, P, _ct.c_int64]
             _syn.synth_jfif_encode.restype = _ct.c_int64
+            _syn.synth_jfif_encode_n.argtypes = [_ct.c_int, _ct.c_int, _ct.c_int, P, P, P, P, P, P, _ct.c_int, P,
+                                                 _ct.c_int64]
+            _syn.synth_jfif_encode_n.restype = _ct.c_int64
             _syn.synth_make_coefs.argtypes = [_ct.c_int, _ct.c_int, P, P, _ct.c_uint64, _ct.c_int, _ct.c_double,
                                               _ct.c_double, P, P, _ct.c_int]
             _syn.synth_make_coefs.restype = _ct.c_int
@@ -205,23 +208,32 @@ def encode_jfif(img: CoefImage, restart_interval: int = 0) -> bytes:
             raise ValueError("coefficients outside the 8-bit baseline range")
     planes = [np.ascontiguousarray(p, np.int16) for p in img.planes]
     qt = [np.ascontiguousarray(q, np.uint16) for q in img.qtabs]
-    hs = np.array(img.h_samp, np.int32)
-    vs = np.array(img.v_samp, np.int32)
-    bw = np.array([p.shape[1] for p in planes], np.int32)
-    bh = np.array([p.shape[0] for p in planes], np.int32)
-    pp = np.array([p.ctypes.data for p in planes], np.uint64)
-    qp = np.array([q.ctypes.data for q in qt], np.uint64)
+    ncomp = len(planes)   # 3, or 1 for a grayscale image
+    hs = np.array(list(img.h_samp)[:3] + [1] * (3 - len(img.h_samp)), np.int32)
+    vs = np.array(list(img.v_samp)[:3] + [1] * (3 - len(img.v_samp)), np.int32)
+    bw = np.array([p.shape[1] for p in planes] + [0] * (3 - ncomp), np.int32)
+    bh = np.array([p.shape[0] for p in planes] + [0] * (3 - ncomp), np.int32)
+    pp = np.array([p.ctypes.data for p in planes] + [0] * (3 - ncomp), np.uint64)
+    qp = np.array([q.ctypes.data for q in qt] + [0] * (3 - ncomp), np.uint64)
     cap = max(4096, sum(p.size for p in planes) * 2)
     while True:
         out = np.empty(cap, np.uint8)
-        n = _enc().synth_jfif_encode(img.width, img.height, hs.ctypes.data, vs.ctypes.data,
-                                     pp.ctypes.data, bw.ctypes.data, bh.ctypes.data, qp.ctypes.data,
-                                     int(restart_interval), out.ctypes.data, cap)
+        n = _enc().synth_jfif_encode_n(img.width, img.height, ncomp, hs.ctypes.data, vs.ctypes.data,
+                                       pp.ctypes.data, bw.ctypes.data, bh.ctypes.data, qp.ctypes.data,
+                                       int(restart_interval), out.ctypes.data, cap)
         if n < 0:
             raise ValueError("encoder: inconsistent image description")
         if n <= cap:
             return out[:n].tobytes()
         cap = int(n)
+
+
+def gray_image(img: CoefImage) -> CoefImage:
+    """The luma plane of a 4:4:4 image as a single-component (grayscale) image."""
+    if img.sampling != "444":
+        raise ValueError("grayscale images are taken from 4:4:4 images")
+    return CoefImage(img.width, img.height, "gray", (1, 1, 1), (1, 1, 1), [img.planes[0]], [img.qtabs[0]],
+                     False, dict(img.meta))
 
 
 # ---- batched workload: many images of mixed size and sampling ----------------

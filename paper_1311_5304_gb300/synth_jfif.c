@@ -107,7 +107,7 @@ static void build_optimal(const int64_t freq_in[256], huff_t *h)
 }
 
 typedef struct {
-    int width, height, hs[3], vs[3], bw[3], bh[3], mx, my, restart;
+    int width, height, ncomp, hs[3], vs[3], bw[3], bh[3], mx, my, restart;
     const int16_t *planes[3];
 } enc_t;
 
@@ -124,7 +124,7 @@ static void scan(const enc_t *e, int64_t dcf[2][256], int64_t acf[2][256],
             pred[0] = pred[1] = pred[2] = 0;
         }
         int mcx = (int)(m % e->mx), mcy = (int)(m / e->mx);
-        for (int c = 0; c < 3; c++) {
+        for (int c = 0; c < e->ncomp; c++) {
             int t = c ? 1 : 0;
             for (int v = 0; v < e->vs[c]; v++)
                 for (int h = 0; h < e->hs[c]; h++) {
@@ -168,30 +168,38 @@ static void scan(const enc_t *e, int64_t dcf[2][256], int64_t acf[2][256],
 /* Returns the stream length (may exceed cap: then call again with a larger
  * buffer), or -1 on bad arguments.  Coefficients must lie in [-2047, 2047]
  * (DC differences in [-2047, 2047] as well for 8-bit baseline). */
-int64_t synth_jfif_encode(int width, int height, const int hs[3], const int vs[3],
-                          const int16_t *planes[3], const int bw[3], const int bh[3],
-                          const uint16_t *qtabs[3], int restart, uint8_t *out, int64_t cap)
+int64_t synth_jfif_encode_n(int width, int height, int ncomp, const int hs[3], const int vs[3],
+                            const int16_t *planes[3], const int bw[3], const int bh[3],
+                            const uint16_t *qtabs[3], int restart, uint8_t *out, int64_t cap)
 {
     make_zigzag();
+    if (ncomp != 1 && ncomp != 3) return -1;
     enc_t e;
     memset(&e, 0, sizeof e);
-    e.width = width; e.height = height; e.restart = restart;
+    e.width = width; e.height = height; e.restart = restart; e.ncomp = ncomp;
     int hmax = 1, vmax = 1;
-    for (int c = 0; c < 3; c++) {
+    for (int c = 0; c < ncomp; c++) {
         e.hs[c] = hs[c]; e.vs[c] = vs[c]; e.bw[c] = bw[c]; e.bh[c] = bh[c]; e.planes[c] = planes[c];
         if (hs[c] > hmax) hmax = hs[c];
         if (vs[c] > vmax) vmax = vs[c];
     }
     e.mx = (width + 8 * hmax - 1) / (8 * hmax);
     e.my = (height + 8 * vmax - 1) / (8 * vmax);
-    for (int c = 0; c < 3; c++)
-        if (bw[c] != e.mx * hs[c] || bh[c] != e.my * vs[c]) return -1;
+    if (ncomp == 1) {
+        /* one component: 8x8 MCUs whatever its sampling factors (T.81 A.2.2) */
+        e.hs[0] = e.vs[0] = 1;
+        e.mx = (width + 7) / 8;
+        e.my = (height + 7) / 8;
+    }
+    for (int c = 0; c < ncomp; c++)
+        if (bw[c] != e.mx * e.hs[c] || bh[c] != e.my * e.vs[c]) return -1;
+    const int ntab = ncomp == 1 ? 1 : 2;
 
     static int64_t dcf[2][256], acf[2][256];
     memset(dcf, 0, sizeof dcf); memset(acf, 0, sizeof acf);
     scan(&e, dcf, acf, NULL, NULL, NULL);
     huff_t dch[2], ach[2];
-    for (int t = 0; t < 2; t++) { build_optimal(dcf[t], &dch[t]); build_optimal(acf[t], &ach[t]); }
+    for (int t = 0; t < ntab; t++) { build_optimal(dcf[t], &dch[t]); build_optimal(acf[t], &ach[t]); }
 
     bw_t w = { out, cap, 0, 0, 0, 0 };
     put_u16(&w, 0xFFD8);
@@ -200,7 +208,7 @@ int64_t synth_jfif_encode(int width, int height, const int hs[3], const int vs[3
     put_byte(&w, 'J'); put_byte(&w, 'F'); put_byte(&w, 'I'); put_byte(&w, 'F'); put_byte(&w, 0);
     put_u16(&w, 0x0101); put_byte(&w, 0); put_u16(&w, 1); put_u16(&w, 1); put_byte(&w, 0); put_byte(&w, 0);
     /* DQT: one table per component (zig-zag order) */
-    for (int c = 0; c < 3; c++) {
+    for (int c = 0; c < ncomp; c++) {
         int big = 0;
         for (int k = 0; k < 64; k++) if (qtabs[c][k] > 255) big = 1;
         put_u16(&w, 0xFFDB); put_u16(&w, 2 + 1 + (big ? 128 : 64));
@@ -211,11 +219,11 @@ int64_t synth_jfif_encode(int width, int height, const int hs[3], const int vs[3
         }
     }
     /* SOF0 */
-    put_u16(&w, 0xFFC0); put_u16(&w, 8 + 3 * 3); put_byte(&w, 8);
-    put_u16(&w, height); put_u16(&w, width); put_byte(&w, 3);
-    for (int c = 0; c < 3; c++) { put_byte(&w, c + 1); put_byte(&w, (hs[c] << 4) | vs[c]); put_byte(&w, c); }
+    put_u16(&w, 0xFFC0); put_u16(&w, 8 + 3 * ncomp); put_byte(&w, 8);
+    put_u16(&w, height); put_u16(&w, width); put_byte(&w, ncomp);
+    for (int c = 0; c < ncomp; c++) { put_byte(&w, c + 1); put_byte(&w, (e.hs[c] << 4) | e.vs[c]); put_byte(&w, c); }
     /* DHT */
-    for (int t = 0; t < 2; t++)
+    for (int t = 0; t < ntab; t++)
         for (int cls = 0; cls < 2; cls++) {
             const huff_t *h = cls ? &ach[t] : &dch[t];
             put_u16(&w, 0xFFC4); put_u16(&w, 2 + 1 + 16 + h->nval);
@@ -225,10 +233,17 @@ int64_t synth_jfif_encode(int width, int height, const int hs[3], const int vs[3
         }
     if (restart) { put_u16(&w, 0xFFDD); put_u16(&w, 4); put_u16(&w, restart); }
     /* SOS */
-    put_u16(&w, 0xFFDA); put_u16(&w, 6 + 2 * 3); put_byte(&w, 3);
-    for (int c = 0; c < 3; c++) { put_byte(&w, c + 1); put_byte(&w, c ? 0x11 : 0x00); }
+    put_u16(&w, 0xFFDA); put_u16(&w, 6 + 2 * ncomp); put_byte(&w, ncomp);
+    for (int c = 0; c < ncomp; c++) { put_byte(&w, c + 1); put_byte(&w, c ? 0x11 : 0x00); }
     put_byte(&w, 0); put_byte(&w, 63); put_byte(&w, 0);
     scan(&e, NULL, NULL, dch, ach, &w);
     put_u16(&w, 0xFFD9);
     return w.n;
+}
+
+int64_t synth_jfif_encode(int width, int height, const int hs[3], const int vs[3],
+                          const int16_t *planes[3], const int bw[3], const int bh[3],
+                          const uint16_t *qtabs[3], int restart, uint8_t *out, int64_t cap)
+{
+    return synth_jfif_encode_n(width, height, 3, hs, vs, planes, bw, bh, qtabs, restart, out, cap);
 }

@@ -98,3 +98,17 @@ def test_threaded_decode_rejects_truncated_stream():
     planes = [np.zeros((info.blocks_h[c], info.blocks_w[c], 64), np.int16) for c in range(3)]
     with pytest.raises(jdec.JdecError):
         jdec.entropy_decode(data[: len(data) // 2], planes, threads=4)
+
+
+@pytest.mark.parametrize("restart", [0, 1, 9])
+def test_grayscale_streams(restart):
+    src = synth.make_image(301, 203, "444", 85, seed=19, kind="texture", sigma=4)
+    img = synth.gray_image(src)
+    data = synth.encode_jfif(img, restart)
+    info = jdec.jpeg_parse(data)
+    assert info.ncomp == 1 and (info.width, info.height) == (301, 203)
+    assert (info.blocks_w[0], info.blocks_h[0]) == img.planes[0].shape[1::-1]
+    for threads in (1, 4):
+        plane = np.zeros((info.blocks_h[0], info.blocks_w[0], 64), np.int16)
+        jdec.entropy_decode(data, [plane], threads=threads)
+        assert np.array_equal(plane, img.planes[0])

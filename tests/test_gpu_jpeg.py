@@ -71,3 +71,20 @@ def test_malformed_stream_is_rejected(ctx):
     # still usable
     ctx.decode_jpeg(data, buf)
     ctx.sync()
+
+
+@pytest.mark.parametrize("restart", [0, 1])
+def test_grayscale_stream(ctx, orc, restart):
+    src = synth.make_image(777, 515, "444", 88, seed=29, kind="texture", sigma=4)
+    img = synth.gray_image(src)
+    mx = img.planes[0].shape[1]
+    data = synth.encode_jfif(img, mx * restart)
+    want = orc.backend_decode_gray(img.width, img.height, img.planes[0], img.qtabs[0])
+    for threads in (1, 8):
+        buf = _rgb(img.height, img.width, pad=3)
+        ctx.decode_jpeg(data, buf, threads=threads)
+        ctx.sync()
+        host = buf.cpu().numpy()
+        assert_same(host[:, :3 * img.width].reshape(img.height, img.width, 3), want,
+                    f"gray restart={restart} threads={threads}")
+        assert np.all(host[:, 3 * img.width:] == POISON)

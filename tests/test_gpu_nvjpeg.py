@@ -87,3 +87,11 @@ def test_gpu_path_equals_nvjpeg(nvj, sampling):
         ctx.sync()
         got = out.cpu().numpy()
     assert_same(got, nvjpeg_decode(nvj, data, img.width, img.height), f"GPU path vs nvJPEG {sampling}")
+
+
+def test_grayscale_equals_nvjpeg(orc, nvj):
+    src = synth.make_image(733, 517, "444", 90, seed=43, kind="texture", sigma=4)
+    img = synth.gray_image(src)
+    data = synth.encode_jfif(img)
+    want = orc.backend_decode_gray(img.width, img.height, img.planes[0], img.qtabs[0])
+    assert_same(want, nvjpeg_decode(nvj, data, img.width, img.height), "gray oracle vs nvJPEG")

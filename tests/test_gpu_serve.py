@@ -106,3 +106,33 @@ def test_request_larger_than_budget_is_rejected(ctx):
         srv.close()
     by = {r.rid: r for r in srv.finished}
     assert by[1].error is None and by[2].error is not None
+
+
+def test_grayscale_requests_in_the_mix(ctx, orc):
+    # grayscale and colour JPEG requests share batches; each equals the oracle
+    import time
+    grays = []
+    for k in range(3):
+        src = synth.make_image(200 + 37 * k, 150 + 11 * k, "444", 85, seed=90 + k, kind="texture", sigma=4)
+        g = synth.gray_image(src)
+        grays.append((synth.encode_jfif(g), g))
+    colour = serve.request_pool(82, per_class=(2, 2, 0), mix=MIX)
+    srv = serve.Server(ctx, hbm_budget_bytes=64 << 20, keep_results=True)
+    try:
+        now = time.perf_counter()
+        rid = 0
+        for data, _ in grays:
+            srv.submit(serve.Request(rid, now, data=data))
+            rid += 1
+        for cls in colour[:2]:
+            for data in cls:
+                srv.submit(serve.Request(rid, now, data=data))
+                rid += 1
+        assert srv.drain(60)
+    finally:
+        srv.close()
+    by = {r.rid: r for r in srv.finished}
+    assert all(r.error is None for r in by.values())
+    for i, (_, g) in enumerate(grays):
+        want = orc.backend_decode_gray(g.width, g.height, g.planes[0], g.qtabs[0])
+        assert np.array_equal(by[i].rgb.cpu().numpy(), want), i
