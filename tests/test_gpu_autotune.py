@@ -1,0 +1,45 @@
+"""Strip-width autotuner: the first image of each (variant, size class) is
+timed at the candidate widths and the fastest is kept and saved; results stay
+bit-exact, the table is written as JSON for this GPU, and a new context
+loading it decodes the same bytes with the tuned width."""
+import json
+
+import numpy as np
+import pytest
+
+from paper_1311_5304_gb300 import jdec, synth
+from gpu_util import assert_same, gpu_rgb, oracle_rgb
+
+pytestmark = pytest.mark.gpu
+
+CANDIDATES = {4, 6, 8, 10, 12, 16, 20, 21, 24, 31, 32, 42}
+
+
+def test_autotune_writes_table_and_stays_exact(orc, tmp_path):
+    path = tmp_path / "tune.json"
+    imgs = [synth.make_image(2048, 1536, s, 85, seed=61, kind="texture", sigma=4, fancy=True)
+            for s in ("444", "422", "420")]
+    with jdec.Context(autotune=True, tune_file=str(path)) as ctx:
+        for img in imgs:
+            got, _, _ = gpu_rgb(ctx, img)
+            assert_same(got, oracle_rgb(orc, img), f"autotuned {img.sampling}")
+    table = json.loads(path.read_text())
+    import torch
+    assert table["sms"] == torch.cuda.get_device_properties(0).multi_processor_count
+    entries = table["entries"]
+    assert {e[0] for e in entries} == {0, 2, 4}   # 4:4:4, 4:2:2 and 4:2:0 triangular
+    assert all(e[2] in CANDIDATES for e in entries)
+    # a second context loads the table (no tuning) and decodes the same bytes
+    with jdec.Context(tune_file=str(path)) as ctx2:
+        for img in imgs:
+            got, _, _ = gpu_rgb(ctx2, img)
+            assert_same(got, oracle_rgb(orc, img), f"loaded table {img.sampling}")
+
+
+def test_table_of_another_gpu_is_ignored(orc, tmp_path):
+    path = tmp_path / "tune.json"
+    path.write_text(json.dumps({"gpu": "other", "sms": 7, "entries": [[v, sc, 1] for v in range(5) for sc in range(20)]}))
+    img = synth.make_image(640, 480, "420", 80, seed=3, kind="texture", sigma=4, fancy=True)
+    with jdec.Context(tune_file=str(path)) as ctx:
+        got, _, _ = gpu_rgb(ctx, img)
+    assert_same(got, oracle_rgb(orc, img), "foreign table")
