@@ -198,6 +198,33 @@ def make_image(width, height, sampling, planes, qtabs, rgb, rgb_pitch=None, fanc
     return im
 
 
+def make_image_flat(width, height, sampling, base_ptr: int, shapes, qtabs, rgb_ptr: int, rgb_pitch: int,
+                    fancy=True, keep=None) -> Image:
+    """Fills a ``jdec_image`` whose planes lie one after another in one device
+    buffer starting at ``base_ptr`` (shapes: (blocks_h, blocks_w) per plane;
+    3 planes, or 1 for grayscale); ``rgb_ptr``: device RGB buffer."""
+    ncomp = len(shapes)
+    hs, vs = ((1, 1, 1), (1, 1, 1)) if ncomp == 1 else (SAMPLINGS[sampling] if isinstance(sampling, str) else sampling)
+    im = Image()
+    im.width, im.height, im.ncomp = int(width), int(height), ncomp
+    keep = keep if keep is not None else []
+    off = 0
+    for c in range(3):
+        im.h_samp[c], im.v_samp[c] = int(hs[c]), int(vs[c])
+    for c in range(ncomp):
+        bh, bw = int(shapes[c][0]), int(shapes[c][1])
+        im.coef[c] = base_ptr + off
+        off += bh * bw * 128
+        im.blocks_h[c], im.blocks_w[c] = bh, bw
+        q = np.ascontiguousarray(np.asarray(qtabs[c]).reshape(64), np.uint16)
+        keep.append(q)
+        im.qtab[c] = q.ctypes.data
+    im.rgb = int(rgb_ptr)
+    im.rgb_pitch = int(rgb_pitch)
+    im.flags = UPSAMPLE_FANCY if fancy else UPSAMPLE_REPLICATE
+    return im
+
+
 class Context:
     """One ``jdec_ctx`` (not thread-safe: one per host thread)."""
 

@@ -47,6 +47,8 @@ class Request:
     sampling: tuple = ()
     qtabs: list = field(default_factory=list)
     host_planes: list = field(default_factory=list)
+    host_buf: object = None              # the planes' single page-locked buffer (planes are views)
+    dev_buf: object = None               # its device copy
     dev_planes: list = field(default_factory=list)
     rgb: object = None                   # device RGB (H, W, 3) uint8
     dev_bytes: int = 0
@@ -87,6 +89,16 @@ class Server:
         self.t0_host = time.perf_counter()
 
     # ---- host side ------------------------------------------------------------
+    @staticmethod
+    def _plane_views(buf, shapes):
+        """Consecutive views of one flat buffer with the given plane shapes."""
+        views, off = [], 0
+        for (bh, bw) in shapes:
+            n = bh * bw * 64
+            views.append(buf[off:off + n].view(bh, bw, 64))
+            off += n
+        return views
+
     def _host_decode(self, req: Request) -> Request:
         torch = self.torch
         if req.coefs is not None:
@@ -95,36 +107,46 @@ class Server:
             req.sampling = (im.h_samp, im.v_samp)
             req.qtabs = im.qtabs
             req.host_planes = im.planes          # already page-locked (torch) or numpy
+            req.host_buf = getattr(im, "host_buf", None)
             return req
         info = jdec.jpeg_parse(req.data)
         req.width, req.height = info.width, info.height
         req.sampling = (tuple(info.h_samp), tuple(info.v_samp)) if info.ncomp == 3 else "gray"
         req.qtabs = [np.array(info.qtab[c][:], np.uint16) for c in range(info.ncomp)]
-        planes = [torch.empty((info.blocks_h[c], info.blocks_w[c], 64), dtype=torch.int16, pin_memory=True)
-                  for c in range(info.ncomp)]
+        shapes = [(info.blocks_h[c], info.blocks_w[c]) for c in range(info.ncomp)]
+        req.host_buf = torch.empty(sum(h * w * 64 for h, w in shapes), dtype=torch.int16, pin_memory=True)
+        planes = self._plane_views(req.host_buf, shapes)
         jdec.entropy_decode(req.data, planes)
         req.host_planes = planes
         return req
 
     def submit(self, req: Request) -> None:
+        if req.coefs is not None and not self.decoding:
+            # nothing to decode on the host: ready at once, in arrival order
+            self._host_decode(req)
+            self._ready_or_reject(req)
+            return
         self.decoding.append((req, self.pool.submit(self._host_decode, req)))
 
     @staticmethod
     def footprint(req: Request) -> int:
-        return sum(int(np.prod(p.shape)) * 2 for p in req.host_planes) + 3 * req.width * req.height
+        return sum(p.shape[0] * p.shape[1] * 128 for p in req.host_planes) + 3 * req.width * req.height
 
     # ---- scheduler steps ------------------------------------------------------
+    def _ready_or_reject(self, req: Request):
+        req.dev_bytes = self.footprint(req)
+        if req.dev_bytes > self.budget:
+            req.error = "request larger than the HBM budget"
+            self.finished.append(req)
+        else:
+            self.ready.append(req)
+
     def _collect_decoded(self):
         while self.decoding and self.decoding[0][1].done():
             req, fut = self.decoding.popleft()
             try:
                 fut.result()
-                req.dev_bytes = self.footprint(req)
-                if req.dev_bytes > self.budget:
-                    req.error = "request larger than the HBM budget"
-                    self.finished.append(req)
-                else:
-                    self.ready.append(req)
+                self._ready_or_reject(req)
             except Exception as e:   # a malformed stream fails only its own request
                 req.error = str(e)
                 self.finished.append(req)
@@ -136,9 +158,13 @@ class Server:
                 req = self.ready.popleft()
                 self.used += req.dev_bytes
                 self.peak_used = max(self.peak_used, self.used)
-                req.dev_planes = [p.to(self.dev, non_blocking=True) if isinstance(p, torch.Tensor)
-                                  else torch.from_numpy(np.ascontiguousarray(p)).to(self.dev, non_blocking=True)
-                                  for p in req.host_planes]
+                if req.host_buf is not None:
+                    # one copy for all planes (descriptors point into it)
+                    req.dev_buf = req.host_buf.to(self.dev, non_blocking=True)
+                else:
+                    req.dev_planes = [p.to(self.dev, non_blocking=True) if isinstance(p, torch.Tensor)
+                                      else torch.from_numpy(np.ascontiguousarray(p)).to(self.dev, non_blocking=True)
+                                      for p in req.host_planes]
                 req.rgb = torch.empty((req.height, req.width, 3), dtype=torch.uint8, device=self.dev)
                 req.copy_event = torch.cuda.Event()
                 req.copy_event.record(self.copy_stream)
@@ -150,12 +176,18 @@ class Server:
         torch = self.torch
         batch, self.admitted = self.admitted[:self.max_batch], self.admitted[self.max_batch:]
         keep = []
-        descs = [jdec.make_image(r.width, r.height, r.sampling, r.dev_planes, r.qtabs, r.rgb, fancy=r.fancy,
+        descs = [jdec.make_image_flat(r.width, r.height, r.sampling, r.dev_buf.data_ptr(),
+                                      [p.shape[:2] for p in r.host_planes], r.qtabs, r.rgb.data_ptr(),
+                                      3 * r.width, fancy=r.fancy, keep=keep) if r.dev_buf is not None else
+                 jdec.make_image(r.width, r.height, r.sampling, r.dev_planes, r.qtabs, r.rgb, fancy=r.fancy,
                                  keep=keep) for r in batch]
         for r in batch:
             self.comp_stream.wait_event(r.copy_event)
-            for p in r.dev_planes:
-                p.record_stream(self.comp_stream)
+            if r.dev_buf is not None:
+                r.dev_buf.record_stream(self.comp_stream)
+            else:
+                for p in r.dev_planes:
+                    p.record_stream(self.comp_stream)
             r.rgb.record_stream(self.comp_stream)
         self.ctx.decode_batch(descs, self.comp_stream)
         ev = torch.cuda.Event(enable_timing=True)
@@ -170,7 +202,9 @@ class Server:
                 r.done_time = done
                 self.used -= r.dev_bytes
                 r.dev_planes = []
+                r.dev_buf = None
                 r.host_planes = []
+                r.host_buf = None
                 if not self.keep:
                     r.rgb = None
                 self.finished.append(r)
@@ -219,7 +253,13 @@ def request_pool(seed: int, per_class=(16, 8, 4), mode: str = "full", mix=SERVE_
             if mode == "full":
                 items.append(synth.encode_jfif(img))
             else:
-                img.planes = [torch.from_numpy(p).pin_memory() for p in img.planes]
+                # page-locked planes in one buffer (one copy per request)
+                buf = torch.empty(sum(p.size for p in img.planes), dtype=torch.int16).pin_memory()
+                views = Server._plane_views(buf, [p.shape[:2] for p in img.planes])
+                for v, p in zip(views, img.planes):
+                    v.copy_(torch.from_numpy(p))
+                img.planes = views
+                img.host_buf = buf
                 items.append(img)
         pool.append(items)
     return pool
