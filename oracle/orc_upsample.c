@@ -20,6 +20,11 @@
  *                                              far clamped to [0, ch-1])
  *   Out[2i]   = (3 S[i] + S[i-1] + 8) >> 4
  *   Out[2i+1] = (3 S[i] + S[i+1] + 7) >> 4   (S index clamped to [0, cw-1])
+ * Vertical factor 2 alone (h1v2, 4:4:0; not in the paper either): Alg. 1
+ * turned vertical, the same weights and alternating biases:
+ *   Out[x][2j]   = (3 C[x][j] + C[x][j-1] + 1) >> 2
+ *   Out[x][2j+1] = (3 C[x][j] + C[x][j+1] + 2) >> 2   (row index clamped to
+ *                                                     [0, ch-1])
  * Replication: Out(x, y) = C[x / sx][y / sy].
  */
 #include "orc.h"
@@ -62,8 +67,11 @@ void orc_upsample_rows(const uint8_t *in, int cw, int ch, int64_t in_pitch,
                     v = (3 * s + sr + 7) >> 4;
                 }
             } else {
-                /* sx == 1, sy == 2 (h1v2) is not a sampling this back-end takes */
-                v = in[(int64_t)(oy / sy) * in_pitch + ox];
+                /* h1v2: Alg. 1 along columns */
+                int j = oy >> 1;
+                int c = in[(int64_t)j * in_pitch + ox];
+                if ((oy & 1) == 0) v = (3 * c + in[(int64_t)clampi(j - 1, 0, ch - 1) * in_pitch + ox] + 1) >> 2;
+                else               v = (3 * c + in[(int64_t)clampi(j + 1, 0, ch - 1) * in_pitch + ox] + 2) >> 2;
             }
             out[(int64_t)oy * out_pitch + ox] = (uint8_t)v;
         }

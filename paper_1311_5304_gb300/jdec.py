@@ -21,7 +21,8 @@ _lib = None
 OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, EBUSY, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 UPSAMPLE_FANCY, UPSAMPLE_REPLICATE = 0, 1
 TEST_WITHHOLD_LOADS = 0x80000000   # testing aid: the kernel's bounded waits run out (JDEC_ETIMEOUT)
-SAMPLINGS = {"444": ((1, 1, 1), (1, 1, 1)), "422": ((2, 1, 1), (1, 1, 1)), "420": ((2, 1, 1), (2, 1, 1))}
+SAMPLINGS = {"444": ((1, 1, 1), (1, 1, 1)), "422": ((2, 1, 1), (1, 1, 1)), "420": ((2, 1, 1), (2, 1, 1)),
+             "440": ((1, 1, 1), (2, 1, 1))}
 
 
 class JdecError(RuntimeError):

@@ -52,6 +52,7 @@ SAMPLINGS = {
     "444": ((1, 1, 1), (1, 1, 1)),
     "422": ((2, 1, 1), (1, 1, 1)),
     "420": ((2, 1, 1), (2, 1, 1)),
+    "440": ((1, 1, 1), (2, 1, 1)),
 }
 
 

@@ -35,6 +35,12 @@ def naive_decode(orc, img):
             return sample(c, x, y)
         if not img.fancy:
             return sample(c, x // sx, y // sy)
+        if sx == 1:
+            # h1v2: the Alg. 1 weights along the column
+            j = y // 2
+            nb = j - 1 if y % 2 == 0 else j + 1
+            bias = 1 if y % 2 == 0 else 2
+            return (3 * sample(c, x, j) + sample(c, x, cl(nb, ch)) + bias) >> 2
         i = x // 2
         nb = i - 1 if x % 2 == 0 else i + 1
         if sy == 1:
@@ -58,7 +64,7 @@ def naive_decode(orc, img):
     return out
 
 
-@pytest.mark.parametrize("sampling", ["444", "422", "420"])
+@pytest.mark.parametrize("sampling", ["444", "422", "420", "440"])
 @pytest.mark.parametrize("fancy", [False, True])
 def test_backend_equals_naive_per_pixel(orc, sampling, fancy):
     rng = np.random.default_rng(zlib.crc32(f"{sampling}{fancy}".encode()))

@@ -93,7 +93,7 @@ def test_h2v1_fancy_crosses_block_boundaries(orc):
 
 # ---- invariants shared by all upsamplers --------------------------------------
 
-@pytest.mark.parametrize("sx,sy", [(2, 1), (2, 2), (1, 1)])
+@pytest.mark.parametrize("sx,sy", [(2, 1), (2, 2), (1, 1), (1, 2)])
 @pytest.mark.parametrize("fancy", [False, True])
 def test_constant_in_constant_out(orc, sx, sy, fancy):
     for v in (0, 1, 77, 254, 255):
@@ -101,7 +101,7 @@ def test_constant_in_constant_out(orc, sx, sy, fancy):
         assert np.all(orc.upsample(p, sx, sy, fancy) == v)
 
 
-@pytest.mark.parametrize("sx,sy", [(2, 1), (2, 2)])
+@pytest.mark.parametrize("sx,sy", [(2, 1), (2, 2), (1, 2)])
 def test_replicate_is_nearest_neighbour(orc, sx, sy):
     rng = np.random.default_rng(3)
     p = rng.integers(0, 256, size=(9, 13)).astype(np.uint8)
@@ -143,6 +143,27 @@ def test_fancy_output_between_its_sources(orc, sy):
             cols = {i, min(max(i + (1 if ox & 1 else -1), 0), cw - 1)}
             src = [p[r, c] for r in rows for c in cols]
             assert min(src) <= out[oy, ox] <= max(src)
+
+
+def test_h1v2_is_h2v1_transposed(orc):
+    # The vertical-only filter is the horizontal one of Alg. 1 turned by 90
+    # degrees: upsampling the transpose must give the transposed output.
+    rng = np.random.default_rng(13)
+    p = rng.integers(0, 256, size=(9, 14)).astype(np.uint8)
+    v = orc.upsample(p, 1, 2, True)
+    h = orc.upsample(np.ascontiguousarray(p.T), 2, 1, True)
+    assert v.shape == (18, 14)
+    assert np.array_equal(v, h.T)
+
+
+def test_h1v2_vertical_ramp_exact(orc):
+    # slope 4 per chroma row: each output row sits 1/4 row from its nearest
+    # source row, where the 3:1 filter is exact (interior rows)
+    y = np.arange(10)
+    p = np.tile((20 + 4 * y).astype(np.uint8)[:, None], (1, 5))
+    out = orc.upsample(p, 1, 2, True).astype(float)
+    ys = np.arange(2, 18)
+    assert np.array_equal(out[ys, 3], 20 + 4 * (ys - 0.5) / 2)
 
 
 def test_h2v2_edges_replicate_true_edge(orc):
