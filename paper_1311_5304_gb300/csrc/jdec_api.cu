@@ -135,11 +135,11 @@ jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers, bool
     if (img->h_samp[1] != 1 || img->v_samp[1] != 1 || img->h_samp[2] != 1 || img->v_samp[2] != 1)
         return JDEC_EUNSUPPORTED;
     const int hm = img->h_samp[0], vm = img->v_samp[0];
-    if (!((hm == 1 && vm == 1) || (hm == 2 && vm == 1) || (hm == 2 && vm == 2))) return JDEC_EUNSUPPORTED;
+    if (hm > 2 || vm > 2) return JDEC_EUNSUPPORTED;   // 4:4:4, 4:2:2, 4:2:0, 4:4:0
     if (img->flags & ~(JDEC_UPSAMPLE_REPLICATE | JDEC_TEST_WITHHOLD_LOADS)) return JDEC_EINVAL;
     if ((img->flags & JDEC_TEST_WITHHOLD_LOADS) && !allow_test) return JDEC_EINVAL;
     g->hm = hm; g->vm = vm;
-    g->fancy = (img->flags & JDEC_UPSAMPLE_REPLICATE) == 0 && hm == 2;
+    g->fancy = (img->flags & JDEC_UPSAMPLE_REPLICATE) == 0 && (hm == 2 || vm == 2);
     g->W = img->width; g->H = img->height;
     g->mcus_x = (img->width + 8 * hm - 1) / (8 * hm);
     g->mcus_y = (img->height + 8 * vm - 1) / (8 * vm);
@@ -163,7 +163,10 @@ jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers, bool
 // of the IDCT threads, and the colour tasks whole rounds of the colour threads.
 int default_wt(const Geometry &g)
 {
-    if (g.hm == 1) return 32;                 // 3 blocks per MCU: 96 blocks
+    if (g.hm == 1 && g.vm == 1) return 32;    // 3 blocks per MCU: 96 blocks
+    // 4:4:0, 4 blocks per MCU: 128; triangular at 28 keeps four CTAs per SM
+    // with its four chroma slots
+    if (g.hm == 1) return g.fancy ? 28 : 32;
     if (g.vm == 1) return g.fancy ? 31 : 32;  // 4 blocks per MCU (+ 4 halo blocks): 128
     return g.fancy ? 20 : 21;                 // 6 blocks per MCU (+ 4 halo blocks): 124 / 126
 }
@@ -238,7 +241,7 @@ void fill_desc(ImageDesc *d, const jdec_image *img, const Geometry &g, int wt, i
 
 bool encode_maps(CUtensorMap maps[3], const jdec_image *img, const Geometry &g, int wt)
 {
-    const int halo = g.fancy ? 1 : 0;
+    const int halo = chroma_halo(g.hm, g.fancy);
     if (!encode_plane_map(&maps[0], img->coef[0], img->blocks_w[0], img->blocks_h[0], g.hm * wt, g.vm)) return false;
     if (g.gray) {
         const int16_t *z = zero_plane();
@@ -283,7 +286,7 @@ jdec_status launch_image(jdec_ctx *ctx, const jdec_image *img, const Geometry &g
 
 int occupancy_cached(jdec_ctx *ctx, int hm, int vm, bool fancy, int smem)
 {
-    const int v = (hm == 1) ? 0 : (vm == 1 ? (fancy ? 2 : 1) : (fancy ? 4 : 3));
+    const int v = (hm == 1) ? (vm == 1 ? 0 : (fancy ? 6 : 5)) : (vm == 1 ? (fancy ? 2 : 1) : (fancy ? 4 : 3));
     for (int i = 0; i < ctx->n_occ; ++i)
         if (ctx->occ_key[i][0] == v && ctx->occ_key[i][1] == smem) return ctx->occ_val[i];
     const int o = fused_occupancy(hm, vm, fancy, smem);

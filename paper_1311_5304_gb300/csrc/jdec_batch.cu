@@ -107,10 +107,11 @@ static bool cached_map(BatchState *b, CUtensorMap *out, const int16_t *base, int
 }
 
 // Relative decode cost of one padded pixel per variant (measured on
-// 8192x8192 images: 4:4:4 is the most expensive per pixel).
+// 8192x8192 images: 4:4:4 is the most expensive per pixel; 4:4:0 taken as
+// 4:2:2, which has as many blocks per pixel).
 static double px_weight(int variant)
 {
-    static const double w[5] = {1.12, 0.95, 1.05, 0.9, 1.0};
+    static const double w[kVariants] = {1.12, 0.95, 1.05, 0.9, 1.0, 0.95, 1.0};
     return w[variant];
 }
 
@@ -153,7 +154,7 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
     // ---- per-image strip width, variant class, and per class the union of
     // its images' shared-memory layouts
     std::vector<int> wt(n), var(n), cls_of(n);
-    UnionLayout U[10];
+    UnionLayout U[kClasses];
     memset(U, 0, sizeof(U));
     for (int i = 0; i < n; ++i) {
         const Geometry &g = geo[i];
@@ -173,7 +174,7 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
         u.ybytes = std::max(u.ybytes, L.ybytes);
         u.slot_bytes = std::max(u.slot_bytes, L.slot_bytes);
     }
-    for (int c = 0; c < 10; ++c) {
+    for (int c = 0; c < kClasses; ++c) {
         UnionLayout &u = U[c];
         u.off_y = kStages * u.stage_bytes;
         u.off_c = u.off_y + 2 * u.ybytes;
@@ -186,9 +187,9 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
     // ---- per class: cost-balanced split of its strip-rows over one wave of
     // that class's CTAs
     struct Seg { int img, strip, rows; double row_cost; };
-    std::vector<Seg> segs[10];
-    double total[10] = {0.0};
-    long rows_of[10] = {0};
+    std::vector<Seg> segs[kClasses];
+    double total[kClasses] = {0.0};
+    long rows_of[kClasses] = {0};
     for (int i = 0; i < n; ++i) {
         const Geometry &g = geo[i];
         const int cls = cls_of[i];
@@ -204,7 +205,7 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
     std::vector<ClassLaunch> launches;
     b->items.clear();
     b->first.clear();
-    for (int cls = 0; cls < 10; ++cls) {
+    for (int cls = 0; cls < kClasses; ++cls) {
         if (segs[cls].empty()) continue;
         const int smem = U[cls].total;
         const int occ = batch_class_occupancy(cls, smem);   // also sets the kernel's attributes
@@ -270,7 +271,7 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
         const Geometry &g = geo[i];
         BatchImage &bi = hi[i];
         memset(&bi, 0, sizeof(bi));
-        const int halo = g.fancy ? 1 : 0;
+        const int halo = chroma_halo(g.hm, g.fancy);
         if (!cached_map(b, &bi.tmap[0], imgs[i].coef[0], imgs[i].blocks_w[0], imgs[i].blocks_h[0], g.hm * wt[i], g.vm))
             return JDEC_ECUDA;
         for (int c = 1; c < 3; ++c) {

@@ -14,6 +14,12 @@ namespace jdec {
 constexpr int kMaxWT = 64;          // widest strip (MCUs) a launch accepts
 constexpr int kStages = 2;          // coefficient double buffer
 
+// Kernel variants (sampling x upsampling): 0: 4:4:4, 1/2: 4:2:2, 3/4: 4:2:0,
+// 5/6: 4:4:0 (replicate / triangular); a batch launch class is one variant
+// with or without the 8-bit dequantisation path: class = 2 * variant + q8.
+constexpr int kVariants = 7;
+constexpr int kClasses = 2 * kVariants;
+
 // Error codes a kernel writes to the context's device error word.
 constexpr int kErrTimeout = 1;      // an mbarrier wait gave up
 constexpr int kErrBadWork = 2;      // reserved: a work item that fails validation on device
@@ -51,7 +57,7 @@ struct UnionLayout {
 struct alignas(128) BatchImage {
     CUtensorMap tmap[3];
     ImageDesc desc;
-    int32_t variant;        // 0: 4:4:4, 1: 4:2:2 replicate, 2: 4:2:2 fancy, 3: 4:2:0 replicate, 4: 4:2:0 fancy
+    int32_t variant;        // 0: 4:4:4, 1/2: 4:2:2, 3/4: 4:2:0, 5/6: 4:4:0 (replicate / triangular)
 };
 
 // A run of MCU rows [r0, r1) of one strip of one image.
@@ -84,7 +90,7 @@ __host__ __device__ inline int default_idct_warps(int hm, int vm) { return (void
 // Shared-memory carve-up of one CTA; identical on host and device.
 //   stages : kStages coefficient tiles written by TMA (1024-aligned regions)
 //   y      : 2 luma sample planes (double buffer), (8*VM) x (8*HM*wt) bytes
-//   c      : nslot chroma slots (4 for 4:2:0 triangular filtering, else 2),
+//   c      : nslot chroma slots (4 for 4:2:0 and 4:4:0 triangular filtering, else 2),
 //            each 2 components x 8 rows x lc bytes (halo blocks included)
 //   q      : dequantisation tables, 3 components x 64 int32 (transposed) or
 //            3 x 32 packed-byte words for the dp2a path
@@ -124,12 +130,19 @@ __host__ __device__ inline SmemLayout apply_union(SmemLayout L, const UnionLayou
     return L;
 }
 
-__host__ __device__ inline int default_slots(int hm, int vm, bool fancy) { return (fancy && hm == 2 && vm == 2) ? 4 : 2; }
+// triangular filtering along columns (4:2:0, 4:4:0) keeps a ring of 4 chroma
+// block rows: the rows above, at and below the current one, and the one loading
+__host__ __device__ inline int default_slots(int hm, int vm, bool fancy) { return (void)hm, (fancy && vm == 2) ? 4 : 2; }
+
+// Chroma blocks loaded on each side of a strip: horizontal triangular
+// filtering (4:2:2, 4:2:0) needs one neighbouring block column; the chroma
+// TMA box is wt + 2 * chroma_halo blocks wide.
+__host__ __device__ inline int chroma_halo(int hm, bool fancy) { return (fancy && hm == 2) ? 1 : 0; }
 
 __host__ __device__ inline SmemLayout smem_layout(int hm, int vm, bool fancy, int wt, int nslot)
 {
     SmemLayout L;
-    const int halo = (fancy && hm == 2) ? 1 : 0;
+    const int halo = chroma_halo(hm, fancy);
     L.ny = hm * vm * wt;
     L.nc = wt + 2 * halo;
     L.lc = round_up(8 * L.nc, 16);

@@ -3,7 +3,7 @@
 //   jdec_fused_kernel<HM, VM, FANCY, Q8, UNI>: one image; CTA b runs share b of the
 //     image's strip-rows (see run_share).
 //
-// Variants: (HM, VM) = (1,1) 4:4:4, (2,1) 4:2:2, (2,2) 4:2:0; FANCY selects
+// Variants: (HM, VM) = (1,1) 4:4:4, (2,1) 4:2:2, (2,2) 4:2:0, (1,2) 4:4:0; FANCY selects
 // the triangular filter of Alg. 1 (Sec. 4.2) over replication.
 #include <cuda_runtime.h>
 #include "jdec_work.cuh"
@@ -114,8 +114,12 @@ __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_batch_kernel(
                         : batch_item<2, 1, true, false>(p, bi, it, smem, ps, last, reload); break;
         case 3: ok = q8 ? batch_item<2, 2, false, true>(p, bi, it, smem, ps, last, reload)
                         : batch_item<2, 2, false, false>(p, bi, it, smem, ps, last, reload); break;
-        default: ok = q8 ? batch_item<2, 2, true, true>(p, bi, it, smem, ps, last, reload)
-                         : batch_item<2, 2, true, false>(p, bi, it, smem, ps, last, reload); break;
+        case 4: ok = q8 ? batch_item<2, 2, true, true>(p, bi, it, smem, ps, last, reload)
+                        : batch_item<2, 2, true, false>(p, bi, it, smem, ps, last, reload); break;
+        case 5: ok = q8 ? batch_item<1, 2, false, true>(p, bi, it, smem, ps, last, reload)
+                        : batch_item<1, 2, false, false>(p, bi, it, smem, ps, last, reload); break;
+        default: ok = q8 ? batch_item<1, 2, true, true>(p, bi, it, smem, ps, last, reload)
+                         : batch_item<1, 2, true, false>(p, bi, it, smem, ps, last, reload); break;
         }
         if (!ok) break;
     }
@@ -172,7 +176,8 @@ static int occupancy_class_t(int smem)
 }
 
 // Class = 2 * variant + q8 (variant 0: 4:4:4, 1: 4:2:2 replicate, 2: 4:2:2
-// triangular, 3: 4:2:0 replicate, 4: 4:2:0 triangular).
+// triangular, 3: 4:2:0 replicate, 4: 4:2:0 triangular, 5: 4:4:0 replicate,
+// 6: 4:4:0 triangular).
 cudaError_t launch_batch_class(int cls, const BatchParams &p, int grid, int smem, cudaStream_t s)
 {
     switch (cls) {
@@ -186,6 +191,10 @@ cudaError_t launch_batch_class(int cls, const BatchParams &p, int grid, int smem
     case 7: return launch_class_t<2, 2, false, true>(p, grid, smem, s);
     case 8: return launch_class_t<2, 2, true, false>(p, grid, smem, s);
     case 9: return launch_class_t<2, 2, true, true>(p, grid, smem, s);
+    case 10: return launch_class_t<1, 2, false, false>(p, grid, smem, s);
+    case 11: return launch_class_t<1, 2, false, true>(p, grid, smem, s);
+    case 12: return launch_class_t<1, 2, true, false>(p, grid, smem, s);
+    case 13: return launch_class_t<1, 2, true, true>(p, grid, smem, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -203,6 +212,10 @@ int batch_class_occupancy(int cls, int smem)
     case 7: return occupancy_class_t<2, 2, false, true>(smem);
     case 8: return occupancy_class_t<2, 2, true, false>(smem);
     case 9: return occupancy_class_t<2, 2, true, true>(smem);
+    case 10: return occupancy_class_t<1, 2, false, false>(smem);
+    case 11: return occupancy_class_t<1, 2, false, true>(smem);
+    case 12: return occupancy_class_t<1, 2, true, false>(smem);
+    case 13: return occupancy_class_t<1, 2, true, true>(smem);
     default: return 0;
     }
 }
@@ -240,7 +253,8 @@ template <bool Q8>
 static cudaError_t launch_q(int hm, int vm, bool fancy, bool uni, const DecodeParams &p, int grid, int smem,
                             cudaStream_t s)
 {
-    if (hm == 1) return launch_variant<1, 1, false, Q8>(p, grid, smem, s);
+    if (hm == 1 && vm == 1) return launch_variant<1, 1, false, Q8>(p, grid, smem, s);
+    if (hm == 1) return fancy ? launch_variant<1, 2, true, Q8>(p, grid, smem, s) : launch_variant<1, 2, false, Q8>(p, grid, smem, s);
     if (vm == 1) {
         if (!fancy) return launch_variant<2, 1, false, Q8>(p, grid, smem, s);
         return uni ? launch_variant<2, 1, true, Q8, true>(p, grid, smem, s) : launch_variant<2, 1, true, Q8>(p, grid, smem, s);
@@ -269,7 +283,8 @@ static int occupancy_variant(int smem)
 
 int fused_occupancy(int hm, int vm, bool fancy, int smem)
 {
-    if (hm == 1) return occupancy_variant<1, 1, false>(smem);
+    if (hm == 1 && vm == 1) return occupancy_variant<1, 1, false>(smem);
+    if (hm == 1) return fancy ? occupancy_variant<1, 2, true>(smem) : occupancy_variant<1, 2, false>(smem);
     if (vm == 1) return fancy ? occupancy_variant<2, 1, true>(smem) : occupancy_variant<2, 1, false>(smem);
     return fancy ? occupancy_variant<2, 2, true>(smem) : occupancy_variant<2, 2, false>(smem);
 }

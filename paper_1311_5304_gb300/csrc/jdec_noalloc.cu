@@ -60,7 +60,7 @@ uint8_t *g_dev_addr[64];   // device address of g_static_scratch per device (nul
 // Cost weights per padded pixel (same ratios as the context-owned batch path).
 double static_px_weight(int variant)
 {
-    static const double w[5] = {1.12, 0.95, 1.05, 0.9, 1.0};
+    static const double w[kVariants] = {1.12, 0.95, 1.05, 0.9, 1.0, 0.95, 1.0};
     return w[variant];
 }
 
@@ -154,7 +154,7 @@ jdec_status decode_batch_static(const jdec_image *imgs, int n, cudaStream_t s)
         } else {
             for (int c = 0; c < nctas; ++c) t_cls_items[c] = 0;
         }
-        for (int cls = 0; cls < 10; ++cls) {
+        for (int cls = 0; cls < kClasses; ++cls) {
             double total = 0.0;
             for (int i = 0; i < n; ++i) {
                 const Geometry &g = t_geo[i];

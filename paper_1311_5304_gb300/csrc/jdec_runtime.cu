@@ -17,7 +17,7 @@ namespace jdec {
 
 int variant_of(const Geometry &g)
 {
-    if (g.hm == 1) return 0;
+    if (g.hm == 1) return g.vm == 1 ? 0 : (g.fancy ? 6 : 5);
     if (g.vm == 1) return g.fancy ? 2 : 1;
     return g.fancy ? 4 : 3;
 }

@@ -24,7 +24,7 @@ struct Geometry {
 
 // Autotuned strip width per (variant, size class).
 struct TuneEntry {
-    int variant;     // 0: 4:4:4, 1: 4:2:2 replicate, 2: 4:2:2 fancy, 3: 4:2:0 replicate, 4: 4:2:0 fancy
+    int variant;     // 0: 4:4:4, 1/2: 4:2:2, 3/4: 4:2:0, 5/6: 4:4:0 (replicate / triangular)
     int size_class;  // log2 of the MCU count, bucketed
     int wt;
     int nidct;       // IDCT threads (0: default split)

@@ -55,7 +55,7 @@ struct PipeState {
 template <int HM, int VM, bool FANCY>
 struct Variant {
     static constexpr bool kHalo = FANCY && HM == 2;            // horizontal neighbours
-    static constexpr bool kRing = FANCY && HM == 2 && VM == 2; // vertical neighbours
+    static constexpr bool kRing = FANCY && VM == 2;            // vertical neighbours
     static constexpr int kLA = kRing ? 1 : 0;                  // chroma lookahead rows
     static constexpr int kPro = kRing ? 2 : 0;                 // chroma-only jobs per item
     // every warp may transform and then convert each job (triangular 4:2:2
@@ -115,8 +115,8 @@ __device__ __forceinline__ void cc_task(const ItemDesc &d, const SmemLayout &L, 
     const uint8_t *slot = cslots + (job & (L.nslot - 1)) * L.slot_bytes;
     int Cb[2][8], Cr[2][8];
     if (HM == 1) {
-        // 4:4:4: chroma sample = pixel
-        const uint8_t *cb = slot + py * L.lc + 16 * gt;
+        // 4:4:4: chroma sample = pixel; 4:4:0 replication: chroma row y/2
+        const uint8_t *cb = slot + (VM == 2 ? (py >> 1) : py) * L.lc + 16 * gt;
         const uint4 wb = *reinterpret_cast<const uint4 *>(cb);
         const uint4 wr = *reinterpret_cast<const uint4 *>(cb + 8 * L.lc);
 #pragma unroll
@@ -193,6 +193,48 @@ __device__ __forceinline__ void cc_task_h2v2_pair(const ItemDesc &d, const SmemL
         tri_h2v2(n6, f6, Cr0);
         load6(pd + 8 * L.lc, f6);
         tri_h2v2(n6, f6, Cr1);
+    }
+    uint8_t *out = d.rgb + static_cast<int64_t>(y) * d.pitch + 3 * x0;
+    cc_store8(y0, Cb0, Cr0, out, n, vec);
+    if (y + 1 < d.H) cc_store8(y1, Cb1, Cr1, out + d.pitch, n, vec);
+}
+
+// 4:4:0 triangular filtering (Alg. 1 along columns): one task = 8 pixels of
+// output rows 2m and 2m+1 of MCU row r, near chroma row j = 8r + m, far rows
+// j-1 and j+1 clamped to the image; the slots rotate as in the 4:2:0 pair
+// task.  No horizontal filter: chroma column = pixel column.
+__device__ __forceinline__ void cc_task_h1v2_pair(const ItemDesc &d, const SmemLayout &L, const uint8_t *yplane,
+                                                  const uint8_t *cslots, int job, int r, int mx0, int m, int g)
+{
+    const int x0 = (mx0 + g) * 8;
+    const int y = 16 * r + 2 * m;
+    if (x0 >= d.W || y >= d.H) return;
+    const int n = min(8, d.W - x0);
+    const bool vec = d.aligned8;
+    const int j = 8 * r + m;
+    const uint8_t *slot = cslots + ((job - 1) & 3) * L.slot_bytes;
+    const uint8_t *pn = slot + m * L.lc + 8 * g;
+    const uint8_t *pu = m > 0 ? pn - L.lc
+                      : (j > 0 ? cslots + ((job - 2) & 3) * L.slot_bytes + 7 * L.lc + 8 * g : pn);
+    const uint8_t *pd = j + 1 >= d.ch ? pn
+                      : (m < 7 ? pn + L.lc : cslots + (job & 3) * L.slot_bytes + 8 * g);
+    const uint2 y0 = *reinterpret_cast<const uint2 *>(yplane + 2 * m * L.ypitch + 8 * g);
+    const uint2 y1 = *reinterpret_cast<const uint2 *>(yplane + (2 * m + 1) * L.ypitch + 8 * g);
+    int Cb0[8], Cr0[8], Cb1[8], Cr1[8];
+#pragma unroll
+    for (int comp = 0; comp < 2; ++comp) {
+        const int off = comp * 8 * L.lc;
+        const uint2 wn = *reinterpret_cast<const uint2 *>(pn + off);
+        const uint2 wu = *reinterpret_cast<const uint2 *>(pu + off);
+        const uint2 wd = *reinterpret_cast<const uint2 *>(pd + off);
+        int *c0 = comp ? Cr0 : Cb0, *c1 = comp ? Cr1 : Cb1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t sel = k < 4 ? 0 : 1;
+            const int near = 3 * byte_of(sel ? wn.y : wn.x, k & 3);
+            c0[k] = (near + byte_of(sel ? wu.y : wu.x, k & 3) + 1) >> 2;
+            c1[k] = (near + byte_of(sel ? wd.y : wd.x, k & 3) + 2) >> 2;
+        }
     }
     uint8_t *out = d.rgb + static_cast<int64_t>(y) * d.pitch + 3 * x0;
     cc_store8(y0, Cb0, Cr0, out, n, vec);
@@ -356,7 +398,7 @@ __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const Im
     } else {
         // =================== colour warps ===================
         const int tc = tid - nidct;
-        // tasks: 4:2:0 triangular, 8 pixels of a pair of output rows; else
+        // tasks: 4:2:0 and 4:4:0 triangular, 8 pixels of a pair of output rows; else
         // 16 pixels of one output row
         const int ngroups = V::kRing ? HM * wte : (HM * wte + 1) >> 1;
         const int rows = V::kRing ? 8 : 8 * VM;
@@ -375,8 +417,10 @@ __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const Im
                 const uint8_t *yplane = yplanes + s * L.ybytes;
                 int py = py0, g = g0;
                 while (py < rows) {
-                    if (V::kRing)
+                    if (V::kRing && HM == 2)
                         cc_task_h2v2_pair(d, L, yplane, cslots, j, r, mx0, py, g);
+                    else if (V::kRing)
+                        cc_task_h1v2_pair(d, L, yplane, cslots, j, r, mx0, py, g);
                     else
                         cc_task<HM, VM, FANCY>(d, L, yplane, cslots, j, r, mx0, wte, py, g);
                     py += dpy;
@@ -515,8 +559,10 @@ __device__ bool run_work_unified(const CUtensorMap *tm, const ItemDesc d, const 
             const int r = r0 + k - V::kPro;
             int py = py0, g = g0;
             while (py < rows) {
-                if (V::kRing)
+                if (V::kRing && HM == 2)
                     cc_task_h2v2_pair(d, L, yplane, cslots, j, r, mx0, py, g);
+                else if (V::kRing)
+                    cc_task_h1v2_pair(d, L, yplane, cslots, j, r, mx0, py, g);
                 else
                     cc_task<HM, VM, FANCY>(d, L, yplane, cslots, j, r, mx0, wte, py, g);
                 py += dpy;

@@ -13,7 +13,7 @@ def _decode(data):
     return info, planes
 
 
-@pytest.mark.parametrize("sampling", ["444", "422", "420"])
+@pytest.mark.parametrize("sampling", ["444", "422", "420", "440"])
 @pytest.mark.parametrize("restart", [0, 1, 5])
 def test_matches_encoder_and_oracle(orc, sampling, restart):
     img = synth.make_image(121, 67, sampling, 88, seed=restart + 3, kind="texture", sigma=5)
@@ -75,7 +75,7 @@ def _decode_mt(data, threads):
     return planes
 
 
-@pytest.mark.parametrize("sampling", ["444", "422", "420"])
+@pytest.mark.parametrize("sampling", ["444", "422", "420", "440"])
 @pytest.mark.parametrize("restart_rows", [None, 1, 3])
 def test_threaded_decode_equals_sequential(sampling, restart_rows):
     # restart intervals of whole MCU rows (chunks start at rows), of a

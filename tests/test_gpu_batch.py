@@ -31,7 +31,7 @@ def _descs(imgs, planes, rgbs, keep):
 def _mixed(rng, n, wmax=700, hmax=500):
     imgs = []
     for i in range(n):
-        s = ["420", "422", "444"][i % 3]
+        s = ["420", "422", "444", "440"][i % 4]
         w, h = int(rng.integers(1, wmax)), int(rng.integers(1, hmax))
         im = synth.random_image(rng, w, h, s, fancy=bool(i % 4 != 1), qmax=255 if i % 5 else 65535)
         imgs.append(im)

@@ -25,7 +25,7 @@ def _rgb(h, w, pad=0):
 
 
 @pytest.mark.parametrize("sampling,fancy", [("444", True), ("422", True), ("422", False), ("420", True),
-                                            ("420", False)])
+                                            ("420", False), ("440", True), ("440", False)])
 @pytest.mark.parametrize("restart", ["none", "row", "odd"])
 def test_matches_oracle(ctx, orc, sampling, fancy, restart):
     import torch

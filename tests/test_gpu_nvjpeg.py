@@ -1,6 +1,6 @@
 """External pin: NVIDIA's nvJPEG library (run only, through its public C API)
 decodes the encoder's baseline JFIF streams to exactly the same RGB bytes as
-the oracle with replicated chroma upsampling, for 4:4:4, 4:2:2 and 4:2:0 --
+the oracle with replicated chroma upsampling, for 4:4:4, 4:2:2, 4:2:0 and 4:4:0 --
 an independent implementation of the same integer IDCT (13-bit constants,
 column pass then row pass, the same rounding), replication and 16-bit
 fixed-point colour conversion.  The GPU path, which equals the oracle, then
@@ -66,7 +66,7 @@ def nvjpeg_decode(lib, data, w, h):
         lib.nvjpegDestroy(handle)
 
 
-@pytest.mark.parametrize("sampling", ["444", "422", "420"])
+@pytest.mark.parametrize("sampling", ["444", "422", "420", "440"])
 @pytest.mark.parametrize("quality,sigma", [(50, 8.0), (90, 4.0), (98, 16.0)])
 def test_oracle_equals_nvjpeg(orc, nvj, sampling, quality, sigma):
     img = synth.make_image(733, 517, sampling, quality, seed=41 + quality, kind="texture", sigma=sigma,
@@ -76,7 +76,7 @@ def test_oracle_equals_nvjpeg(orc, nvj, sampling, quality, sigma):
                 f"oracle vs nvJPEG {sampling} q{quality}")
 
 
-@pytest.mark.parametrize("sampling", ["444", "422", "420"])
+@pytest.mark.parametrize("sampling", ["444", "422", "420", "440"])
 def test_gpu_path_equals_nvjpeg(nvj, sampling):
     import torch
     img = synth.make_image(1031, 769, sampling, 85, seed=7, kind="texture", sigma=4, fancy=False)

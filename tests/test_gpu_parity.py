@@ -14,7 +14,7 @@ from gpu_util import assert_padding_untouched, assert_same, gpu_rgb, oracle_rgb,
 
 pytestmark = pytest.mark.gpu
 
-MODES = [("444", True), ("422", False), ("422", True), ("420", False), ("420", True)]
+MODES = [("444", True), ("422", False), ("422", True), ("420", False), ("420", True), ("440", False), ("440", True)]
 
 
 @pytest.fixture(scope="module")
@@ -139,6 +139,7 @@ def test_invalid_descriptions_launch_nothing(ctx):
     assert status(height=70000) == jdec.EINVAL
     assert status(ncomp=1) == jdec.EUNSUPPORTED
     assert status(h_samp=(1, 2)) == jdec.EUNSUPPORTED
+    assert status(h_samp=(0, 3)) == jdec.EUNSUPPORTED
     assert status(flags=7) == jdec.EINVAL
     assert status(rgb=None) == jdec.EINVAL
     keep = []
@@ -150,7 +151,7 @@ def test_invalid_descriptions_launch_nothing(ctx):
     assert ctx.sync(check=False) == jdec.OK
 
 
-@pytest.mark.parametrize("sampling", ["444", "422", "420"])
+@pytest.mark.parametrize("sampling", ["444", "422", "420", "440"])
 def test_config2_full_size_8192(ctx, orc, sampling):
     img = synth.make_image(8192, 8192, sampling, 90, seed=13115304 + 2000, kind="texture", sigma=4.0,
                            cover=0.85, fancy=True)

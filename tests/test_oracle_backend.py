@@ -75,8 +75,8 @@ def test_backend_equals_naive_per_pixel(orc, sampling, fancy):
 
 
 def test_mcu_geometry_follows_sec2():
-    # 4:4:4 MCU is 8x8 px, 4:2:2 is 16x8 px, 4:2:0 is 16x16 px
-    for s, (mw, mh) in {"444": (8, 8), "422": (16, 8), "420": (16, 16)}.items():
+    # 4:4:4 MCU is 8x8 px, 4:2:2 is 16x8 px, 4:2:0 is 16x16 px, 4:4:0 is 8x16 px
+    for s, (mw, mh) in {"444": (8, 8), "422": (16, 8), "420": (16, 16), "440": (8, 16)}.items():
         hs, vs, mx, my = synth.geometry(mw, mh, s)
         assert (mx, my) == (1, 1)
         hs, vs, mx, my = synth.geometry(mw + 1, mh + 1, s)
@@ -85,7 +85,7 @@ def test_mcu_geometry_follows_sec2():
 
 def test_multithreaded_equals_single(orc):
     rng = np.random.default_rng(99)
-    for s in ("444", "422", "420"):
+    for s in ("444", "422", "420", "440"):
         img = synth.random_image(rng, 203, 77, s)
         a = orc.backend_decode(203, 77, img.h_samp, img.v_samp, img.planes, img.qtabs, True)
         b = orc.backend_decode(203, 77, img.h_samp, img.v_samp, img.planes, img.qtabs, True, threads=5)

@@ -18,7 +18,7 @@ def _check(orc, img, restart=0):
     return data
 
 
-@pytest.mark.parametrize("sampling", ["444", "422", "420"])
+@pytest.mark.parametrize("sampling", ["444", "422", "420", "440"])
 @pytest.mark.parametrize("restart", [0, 1, 7])
 def test_round_trip_synthetic(orc, sampling, restart):
     img = synth.make_image(72, 40, sampling, 85, seed=5 + restart, kind="texture", sigma=6)

@@ -20,7 +20,7 @@ def _batch(rng, n, wmax, hmax):
     import torch
     imgs, planes, keep = [], [], []
     for i in range(n):
-        s = ["420", "422", "444"][i % 3]
+        s = ["420", "422", "444", "440"][i % 4]
         im = synth.random_image(rng, int(rng.integers(1, wmax)), int(rng.integers(1, hmax)), s,
                                 fancy=bool(i % 4 != 2), qmax=255 if i % 5 else 65535)
         imgs.append(im)
