@@ -6,7 +6,7 @@
  * fixed-point IDCT as a column pass (Eq. 1) followed by a row pass (Eq. 2)
  * with range-limit clamping (Sec. 4.1), chroma upsampling by replication or
  * by the triangular filter of Alg. 1 (Sec. 4.2; 4:2:2 as printed, 4:2:0 as the
- * separable extension), and YCbCr -> RGB by Alg. 2 in 16-bit fixed point
+ * separable extension, 4:4:0 as Alg. 1 along columns), and YCbCr -> RGB by Alg. 2 in 16-bit fixed point
  * (Sec. 4.3), writing interleaved RGB in raster order (Sec. 4.3, Fig. 3-4).
  * Entropy (Huffman) decoding stays on the host (Sec. 2, Sec. 4.5) and is not
  * part of this interface: callers pass entropy-decoded coefficients.
@@ -19,7 +19,7 @@
  * Hmax = max h_samp, Vmax = max v_samp: MCUs_x = ceil(W / (8*Hmax)),
  * MCUs_y = ceil(H / (8*Vmax)), component c has blocks_w[c] = MCUs_x*h_samp[c]
  * by blocks_h[c] = MCUs_y*v_samp[c] blocks.  The MCU is 8x8 pixels for 4:4:4
- * and 16x8 for 4:2:2 (Sec. 2), 16x16 for 4:2:0.
+ * and 16x8 for 4:2:2 (Sec. 2), 16x16 for 4:2:0, 8x16 for 4:4:0.
  *
  * Output: 8-bit interleaved R,G,B, rgb_pitch bytes between rows; only the
  * W x H pixels are written, padding bytes of a row are left untouched.
@@ -91,7 +91,8 @@ typedef struct {
                                      qtab[0] only, h_samp[0] = v_samp[0] = 1,
                                      blocks = ceil(W/8) x ceil(H/8), output
                                      R = G = B = Y                             */
-    uint8_t h_samp[3], v_samp[3]; /* luma (1,1) | (2,1) | (2,2); chroma (1,1)  */
+    uint8_t h_samp[3], v_samp[3]; /* luma (1,1) | (2,1) | (2,2) | (1,2) (4:4:4,
+                                     4:2:2, 4:2:0, 4:4:0); chroma (1,1)         */
     const int16_t *coef[3];       /* DEVICE pointers, 16-byte aligned, planes
                                      as described above                         */
     int32_t blocks_w[3], blocks_h[3]; /* must equal MCUs_x*h, MCUs_y*v         */
@@ -147,8 +148,9 @@ typedef struct {
 } jdec_jpeg_info;
 
 /* Parses the headers of a JPEG stream (no entropy decoding).  Returns
- * JDEC_EUNSUPPORTED for progressive, arithmetic, 12-bit, or non-3-component
- * streams and JDEC_EINVAL for malformed ones. */
+ * JDEC_EUNSUPPORTED for progressive, arithmetic or 12-bit streams, for
+ * component counts other than 1 and 3 and for sampling factors above 2, and
+ * JDEC_EINVAL for malformed ones. */
 JDEC_API jdec_status jdec_jpeg_parse(const uint8_t *data, size_t size, jdec_jpeg_info *info);
 
 /* Huffman-decodes the stream into natural-order int16 coefficient planes laid
