@@ -20,7 +20,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = ["orc_idct.c", "orc_color.c", "orc_upsample.c", "orc_backend.c", "orc_huffman.c"]
+_SRC = ["orc_idct.c", "orc_idct_aan.c", "orc_color.c", "orc_upsample.c", "orc_backend.c", "orc_huffman.c"]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liborc.so")
 _lock = threading.Lock()
@@ -51,6 +51,7 @@ class OrcImage(ctypes.Structure):
         ("blocks_w", ctypes.c_int32 * 3), ("blocks_h", ctypes.c_int32 * 3),
         ("qtab", ctypes.c_void_p * 3),
         ("fancy", ctypes.c_int32),
+        ("idct", ctypes.c_int32),
     ]
 
 
@@ -74,6 +75,9 @@ def lib():
             _lib.orc_idct_blocks.argtypes = [P, P, P, ctypes.c_int64]
             _lib.orc_idct_core_blocks.argtypes = [P, P, P, ctypes.c_int64]
             _lib.orc_idct_constants.argtypes = [P]
+            _lib.orc_idct_aan_blocks.argtypes = [P, P, P, ctypes.c_int64]
+            _lib.orc_idct_aan_core_blocks.argtypes = [P, P, P, ctypes.c_int64]
+            _lib.orc_idct_aan_constants.argtypes = [P, P]
             _lib.orc_ycc_to_rgb.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
             _lib.orc_ycc_to_rgb_all.argtypes = [P]
             _lib.orc_upsample.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
@@ -81,7 +85,7 @@ def lib():
             _lib.orc_backend_decode.argtypes = [ctypes.POINTER(OrcImage), P, ctypes.c_int64]
             _lib.orc_backend_decode.restype = ctypes.c_int
             _lib.orc_backend_decode_gray.argtypes = [ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32, ctypes.c_int32,
-                                                     P, P, ctypes.c_int64]
+                                                     P, P, ctypes.c_int64, ctypes.c_int32]
             _lib.orc_backend_decode_gray.restype = ctypes.c_int
             _lib.orc_backend_decode_mt.argtypes = [ctypes.POINTER(OrcImage), P, ctypes.c_int64, ctypes.c_int]
             _lib.orc_backend_decode_mt.restype = ctypes.c_int
@@ -104,22 +108,33 @@ def idct_constants() -> np.ndarray:
     return k
 
 
-def idct_blocks(coef: np.ndarray, q: np.ndarray) -> np.ndarray:
-    """coef (n, 64) int16 natural order, q (64,) -> (n, 64) uint8 samples."""
+def idct_blocks(coef: np.ndarray, q: np.ndarray, aan: bool = False) -> np.ndarray:
+    """coef (n, 64) int16 natural order, q (64,) -> (n, 64) uint8 samples
+    (the LLM IDCT, or the AAN one with ``aan``)."""
     coef = np.ascontiguousarray(coef, np.int16).reshape(-1, 64)
     q = np.ascontiguousarray(q, np.uint16).reshape(64)
     out = np.zeros((coef.shape[0], 64), np.uint8)
-    lib().orc_idct_blocks(_ptr(coef), _ptr(q), _ptr(out), coef.shape[0])
+    fn = lib().orc_idct_aan_blocks if aan else lib().orc_idct_blocks
+    fn(_ptr(coef), _ptr(q), _ptr(out), coef.shape[0])
     return out
 
 
-def idct_core_blocks(coef: np.ndarray, q: np.ndarray | None = None) -> np.ndarray:
+def idct_core_blocks(coef: np.ndarray, q: np.ndarray | None = None, aan: bool = False) -> np.ndarray:
     """Rounded 2-D IDCT without level shift / clamp, (n, 64) int32."""
     coef = np.ascontiguousarray(coef, np.int16).reshape(-1, 64)
     q = np.ones(64, np.uint16) if q is None else np.ascontiguousarray(q, np.uint16).reshape(64)
     out = np.zeros((coef.shape[0], 64), np.int32)
-    lib().orc_idct_core_blocks(_ptr(coef), _ptr(q), _ptr(out), coef.shape[0])
+    fn = lib().orc_idct_aan_core_blocks if aan else lib().orc_idct_core_blocks
+    fn(_ptr(coef), _ptr(q), _ptr(out), coef.shape[0])
     return out
+
+
+def idct_aan_constants():
+    """(S (8, 8) int32 scale table [v, u], (K1, K2, K3, K4)) of the AAN IDCT."""
+    s = np.zeros(64, np.int32)
+    k = np.zeros(4, np.int32)
+    lib().orc_idct_aan_constants(_ptr(s), _ptr(k))
+    return s.reshape(8, 8), tuple(int(v) for v in k)
 
 
 # ---- colour conversion ----------------------------------------------------
@@ -149,7 +164,7 @@ def upsample(plane: np.ndarray, sx: int, sy: int, fancy: bool) -> np.ndarray:
 
 # ---- whole back-end -----------------------------------------------------------
 
-def _orc_image(width, height, h_samp, v_samp, planes, qtabs, fancy, keep):
+def _orc_image(width, height, h_samp, v_samp, planes, qtabs, fancy, keep, aan=False):
     img = OrcImage()
     img.width, img.height = int(width), int(height)
     for c in range(3):
@@ -161,13 +176,16 @@ def _orc_image(width, height, h_samp, v_samp, planes, qtabs, fancy, keep):
         img.blocks_h[c], img.blocks_w[c] = int(p.shape[0]), int(p.shape[1])
         img.qtab[c] = _ptr(q)
     img.fancy = int(bool(fancy))
+    img.idct = int(bool(aan))
     return img
 
 
-def backend_decode(width, height, h_samp, v_samp, planes, qtabs, fancy, threads: int = 1) -> np.ndarray:
-    """planes[c]: (blocks_h, blocks_w, 64) int16; returns (H, W, 3) uint8."""
+def backend_decode(width, height, h_samp, v_samp, planes, qtabs, fancy, threads: int = 1,
+                   aan: bool = False) -> np.ndarray:
+    """planes[c]: (blocks_h, blocks_w, 64) int16; returns (H, W, 3) uint8.
+    ``aan`` selects the AAN IDCT instead of the LLM one."""
     keep = []
-    img = _orc_image(width, height, h_samp, v_samp, planes, qtabs, fancy, keep)
+    img = _orc_image(width, height, h_samp, v_samp, planes, qtabs, fancy, keep, aan)
     out = np.zeros((height, width, 3), np.uint8)
     if threads <= 1:
         rc = lib().orc_backend_decode(ctypes.byref(img), _ptr(out), 3 * width)
@@ -179,14 +197,14 @@ def backend_decode(width, height, h_samp, v_samp, planes, qtabs, fancy, threads:
     return out
 
 
-def backend_decode_gray(width, height, plane, qtab) -> np.ndarray:
+def backend_decode_gray(width, height, plane, qtab, aan: bool = False) -> np.ndarray:
     """Single-component image: plane (blocks_h, blocks_w, 64) int16; returns
     (H, W, 3) uint8 with R = G = B = Y."""
     p = np.ascontiguousarray(plane, np.int16)
     q = np.ascontiguousarray(qtab, np.uint16).reshape(64)
     out = np.zeros((height, width, 3), np.uint8)
     rc = lib().orc_backend_decode_gray(int(width), int(height), _ptr(p), int(p.shape[1]), int(p.shape[0]), _ptr(q),
-                                       _ptr(out), 3 * width)
+                                       _ptr(out), 3 * width, int(bool(aan)))
     if rc != 0:
         raise ValueError("oracle: inconsistent grayscale description")
     return out

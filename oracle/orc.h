@@ -14,7 +14,7 @@
  * results are defined for every input, including adversarial coefficients.
  *
  * Parity pins (tests/test_oracle_*.py): double-precision Eq. 1-2, the
- * IEEE 1180-1990 accuracy procedure, the DC-only closed form (exhaustive),
+ * IEEE 1180-1990 accuracy procedure (both IDCT factorisations), the DC-only closed form (exhaustive),
  * DCT->IDCT round trips, Alg. 2 in floating point (exhaustive over 2^24),
  * Alg. 1 as printed, upsampling invariants, and a second naive per-pixel
  * implementation on tiny images.  The particular 13-bit LLM flowgraph is the
@@ -55,6 +55,19 @@ void orc_idct_core_blocks(const int16_t *coef, const uint16_t q[64], int32_t *ou
  * orc_idct.c.  Exposed so a test can pin them to their definitions. */
 void orc_idct_constants(int32_t k[12]);
 
+/* The AAN scaled IDCT (orc_idct_aan.c; the algorithm Sec. 2 names): the same
+ * transform with the scale factors folded into the dequantisation table and
+ * five constant multiplications per 8-point pass, 12 fractional bits.  Same
+ * calling conventions as the four calls above; the core value is
+ * (Y + 2^14) >> 15. */
+void orc_idct_aan_block(const int16_t coef[64], const uint16_t q[64], uint8_t out[64]);
+void orc_idct_aan_core(const int16_t coef[64], const uint16_t q[64], int32_t out[64]);
+void orc_idct_aan_blocks(const int16_t *coef, const uint16_t q[64], uint8_t *out, int64_t n);
+void orc_idct_aan_core_blocks(const int16_t *coef, const uint16_t q[64], int32_t *out, int64_t n);
+/* The integer scale table S(v,u) = round(2^12 s_v s_u) ([v*8+u]) and the four
+ * 32-bit product constants K1..K4 documented in orc_idct_aan.c. */
+void orc_idct_aan_constants(int32_t scale[64], int32_t k[4]);
+
 /* ---- Colour conversion (Sec. 4.3, Alg. 2) ------------------------------ */
 void orc_ycc_to_rgb(int y, int cb, int cr, uint8_t rgb[3]);
 /* Whole-cube form: rgb[((y*256+cb)*256+cr)*3 + c] for all 2^24 inputs. */
@@ -76,6 +89,7 @@ typedef struct {
     int32_t blocks_w[3], blocks_h[3];
     const uint16_t *qtab[3];      /* 64 entries, natural order */
     int32_t fancy;                /* 1: triangular upsampling, 0: replication */
+    int32_t idct;                 /* 0: LLM IDCT (orc_idct.c), 1: AAN (orc_idct_aan.c) */
 } orc_image;
 
 /* Decodes to interleaved RGB, rgb_pitch bytes per row; writes only the
@@ -88,7 +102,8 @@ int orc_backend_decode(const orc_image *img, uint8_t *rgb, int64_t rgb_pitch);
  * triple (Y, Y, Y): the output format is interleaved RGB (Sec. 4.3), and
  * Alg. 2 maps (Y, 128, 128) to (Y, Y, Y).  Returns 0, or -1 if inconsistent. */
 int orc_backend_decode_gray(int32_t width, int32_t height, const int16_t *coef, int32_t blocks_w,
-                            int32_t blocks_h, const uint16_t q[64], uint8_t *rgb, int64_t rgb_pitch);
+                            int32_t blocks_h, const uint16_t q[64], uint8_t *rgb, int64_t rgb_pitch,
+                            int32_t idct);
 
 /* Number of threads used by orc_backend_decode_mt (images are split into
  * bands of output rows; the arithmetic is orc_backend_decode's). */

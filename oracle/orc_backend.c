@@ -80,7 +80,10 @@ static void stage_idct(job *J, int c, int64_t b0, int64_t b1)
     uint8_t blk[64];
     for (int64_t b = b0; b < b1; b++) {
         const int bx = (int)(b % img->blocks_w[c]), by = (int)(b / img->blocks_w[c]);
-        orc_idct_block(img->coef[c] + 64 * b, img->qtab[c], blk);
+        if (img->idct)
+            orc_idct_aan_block(img->coef[c] + 64 * b, img->qtab[c], blk);
+        else
+            orc_idct_block(img->coef[c] + 64 * b, img->qtab[c], blk);
         for (int y = 0; y < 8; y++)
             memcpy(J->plane[c] + (int64_t)(by * 8 + y) * J->ppitch[c] + bx * 8, blk + 8 * y, 8);
     }
@@ -115,14 +118,18 @@ int orc_backend_decode(const orc_image *img, uint8_t *rgb, int64_t rgb_pitch)
 }
 
 int orc_backend_decode_gray(int32_t width, int32_t height, const int16_t *coef, int32_t blocks_w,
-                            int32_t blocks_h, const uint16_t q[64], uint8_t *rgb, int64_t rgb_pitch)
+                            int32_t blocks_h, const uint16_t q[64], uint8_t *rgb, int64_t rgb_pitch,
+                            int32_t idct)
 {
     if (width < 1 || height < 1 || !coef || !q || !rgb || rgb_pitch < 3 * (int64_t)width) return -1;
     if (blocks_w != (width + 7) / 8 || blocks_h != (height + 7) / 8) return -1;
     uint8_t blk[64];
     for (int by = 0; by < blocks_h; by++)
         for (int bx = 0; bx < blocks_w; bx++) {
-            orc_idct_block(coef + 64 * ((int64_t)by * blocks_w + bx), q, blk);
+            if (idct)
+                orc_idct_aan_block(coef + 64 * ((int64_t)by * blocks_w + bx), q, blk);
+            else
+                orc_idct_block(coef + 64 * ((int64_t)by * blocks_w + bx), q, blk);
             for (int y = 0; y < 8; y++) {
                 const int py = by * 8 + y;
                 if (py >= height) break;

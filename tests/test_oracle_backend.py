@@ -12,7 +12,7 @@ from paper_1311_5304_gb300 import synth
 SIZES = [(1, 1), (8, 8), (15, 17), (16, 16), (17, 9), (33, 31), (7, 40)]
 
 
-def naive_decode(orc, img):
+def naive_decode(orc, img, aan=False):
     hs, vs = img.h_samp, img.v_samp
     hmax, vmax = max(hs), max(vs)
     W, H = img.width, img.height
@@ -23,7 +23,7 @@ def naive_decode(orc, img):
         bx, by = i // 8, j // 8
         key = (c, bx, by)
         if key not in cache:
-            cache[key] = orc.idct_blocks(img.planes[c][by, bx][None], img.qtabs[c])[0]
+            cache[key] = orc.idct_blocks(img.planes[c][by, bx][None], img.qtabs[c], aan=aan)[0]
         return int(cache[key][(j % 8) * 8 + (i % 8)])
 
     def comp_value(c, x, y):
@@ -72,6 +72,17 @@ def test_backend_equals_naive_per_pixel(orc, sampling, fancy):
         img = synth.random_image(rng, w, h, sampling, fancy=fancy)
         got = orc.backend_decode(w, h, img.h_samp, img.v_samp, img.planes, img.qtabs, fancy)
         assert np.array_equal(got, naive_decode(orc, img)), (w, h)
+
+
+@pytest.mark.parametrize("sampling", ["444", "420"])
+def test_backend_with_aan_idct_equals_naive_per_pixel(orc, sampling):
+    rng = np.random.default_rng(zlib.crc32(f"aan{sampling}".encode()))
+    for (w, h) in SIZES:
+        img = synth.random_image(rng, w, h, sampling, fancy=True)
+        got = orc.backend_decode(w, h, img.h_samp, img.v_samp, img.planes, img.qtabs, True, aan=True)
+        assert np.array_equal(got, naive_decode(orc, img, aan=True)), (w, h)
+        got_mt = orc.backend_decode(w, h, img.h_samp, img.v_samp, img.planes, img.qtabs, True, threads=3, aan=True)
+        assert np.array_equal(got_mt, got)
 
 
 def test_mcu_geometry_follows_sec2():
