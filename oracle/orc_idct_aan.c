@@ -37,8 +37,10 @@
  *     P3(t) = 3t - hi(t,  K3)   ~ (2c + 2s) t,      K3 = round((3 - 2c - 2s) 2^32)
  *     P4(t) = t  - hi(t, -K4)   ~ (2c - 2s) t,      K4 = round((2c - 2s - 1) 2^32)
  *   both passes use the flowgraph above with these products and no
- *   intermediate descale; the 2-D value is f * 2^15 (12 fractional bits and
- *   the 1/8), so the sample is clamp(((Y + 2^14) >> 15) + 128, 0, 255).
+ *   intermediate descale; the 2-D value Y is f * 2^15 (12 fractional bits and
+ *   the 1/8).  The sample adds the rounding and the level shift in one
+ *   constant, as orc_idct.c does: clamp((Y + 2^14 + 128 * 2^15) >> 15, 0, 255)
+ *   (the same as ((Y + 2^14) >> 15) + 128 unless the sum wraps).
  * Every intermediate is int32 with two's-complement wrap (-fwrapv); hi() takes
  * the high word of the exact 64-bit product.
  */
@@ -130,7 +132,7 @@ void orc_idct_aan_block(const int16_t coef[64], const uint16_t q[64], uint8_t ou
     int32_t Y[64];
     aan2d(coef, q, Y);
     for (int i = 0; i < 64; i++) {
-        const int32_t s = ((Y[i] + (1 << (AAN_SHIFT - 1))) >> AAN_SHIFT) + 128;
+        const int32_t s = (Y[i] + (1 << (AAN_SHIFT - 1)) + (128 << AAN_SHIFT)) >> AAN_SHIFT;
         out[i] = (uint8_t)(s < 0 ? 0 : (s > 255 ? 255 : s));
     }
 }

@@ -272,6 +272,100 @@ __device__ __forceinline__ void idct_block_q8(uint32_t blk, const uint32_t *__re
 }
 
 // ---------------------------------------------------------------------------
+// AAN scaled IDCT (the algorithm Sec. 2 names).  With s_0 = 1 and
+// s_k = sqrt(2) cos(k pi / 16), inputs w_k = s_k X_k make the 8-point
+// transform cost five constant products: even half P = w2 + w6,
+// q = sqrt2 (w2 - w6) - P, e = w0 + w4 +- P, w0 - w4 +- q; odd half
+// a = w5 + w3, b = w5 - w3, c = w1 + w7, d = w1 - w7, o0 = a + c,
+// z = 2cos(pi/8)(b + d), o1 = z - (2cos(pi/8) + 2sin(pi/8)) b - o0,
+// o2 = sqrt2 (c - a) - o1, o3 = z - (2cos(pi/8) - 2sin(pi/8)) d - o2;
+// y[n] = e[n] + o[n], y[7-n] = e[n] - o[n].  The 2-D scale factors
+// s_v s_u * 2^12 are folded into the dequantisation table on the host, so the
+// working values carry 12 fractional bits and need no descale between the
+// passes.  Each product is an integer part plus the high word of a 32-bit
+// fraction (one mad.hi):
+//   sqrt2 t          = t  + hi(t * kA1),  kA1 = round((sqrt2 - 1) 2^32)
+//   2c t             = 2t + hi(t * -kA2), kA2 = round((2 - 2c) 2^32)
+//   (2c + 2s) t      = 3t - hi(t * kA3),  kA3 = round((3 - 2c - 2s) 2^32)
+//   (2c - 2s) t      = t  - hi(t * -kA4), kA4 = round((2c - 2s - 1) 2^32)
+// (c = cos(pi/8), s = sin(pi/8)).  Sample = clamp(((Y + 2^14) >> 15) + 128).
+// ---------------------------------------------------------------------------
+constexpr int kA1 = 1779033704;
+constexpr int kA2 = 653869837;
+constexpr int kA3 = 1661611479;
+constexpr int kA4 = 353871806;
+
+// hi(a * b) + c: the high word of the exact 64-bit product, plus c.
+__device__ __forceinline__ int mad_hi(int a, int b, int c)
+{
+    int d;
+    asm("mad.hi.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// One 8-point AAN transform of scaled inputs; `bias` reaches every output
+// once (it enters through w0, which no product touches).
+__device__ __forceinline__ void idct8_aan(const int w0, const int w1, const int w2, const int w3,
+                                          const int w4, const int w5, const int w6, const int w7,
+                                          const int bias, int y[8])
+{
+    const int t10 = w0 + bias + w4, t11 = w0 + bias - w4;
+    const int P = w2 + w6, D = w2 - w6;
+    const int q = mad_hi(D, kA1, D - P);
+    const int e0 = t10 + P, e3 = t10 - P, e1 = t11 + q, e2 = t11 - q;
+    const int a = w5 + w3, b = w5 - w3, c = w1 + w7, d = w1 - w7;
+    const int o0 = a + c, r = c - a, bd = b + d;
+    const int z = mad_hi(bd, -kA2, 2 * bd);
+    const int o1 = mad_hi(b, kA3, z - 3 * b) - o0;
+    const int o2 = mad_hi(r, kA1, r - o1);
+    const int o3 = mad_hi(d, -kA4, z - d) - o2;
+    y[0] = e0 + o0; y[7] = e0 - o0;
+    y[1] = e1 + o1; y[6] = e1 - o1;
+    y[2] = e2 + o2; y[5] = e2 - o2;
+    y[3] = e3 + o3; y[4] = e3 - o3;
+}
+
+// Dequantise with the prescaled table and run both AAN passes on one block
+// (layout, swizzle and output as idct_block; qt[8*u + v] = Q(v,u) S(v,u)).
+__device__ __forceinline__ void idct_block_aan(uint32_t blk, const int *__restrict__ qt, uint8_t *dst, int pitch)
+{
+    const uint32_t sw = (blk >> 7) & 7u;
+    uint32_t w[8][4];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const uint4 r = lds128(blk + ((static_cast<uint32_t>(v) ^ sw) << 4));
+        w[v][0] = r.x; w[v][1] = r.y; w[v][2] = r.z; w[v][3] = r.w;
+    }
+    int ws[8][8];   // [y][u], 12 fractional bits, scaled by s_u
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int4 qa = *reinterpret_cast<const int4 *>(qt + 8 * u);
+        const int4 qb = *reinterpret_cast<const int4 *>(qt + 8 * u + 4);
+        const int qv[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+        int x[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const uint32_t word = w[v][u >> 1];
+            x[v] = ((u & 1) ? sext_hi(word) : sext_lo(word)) * qv[v];
+        }
+        int y[8];
+        idct8_aan(x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7], 0, y);
+#pragma unroll
+        for (int yy = 0; yy < 8; ++yy) ws[yy][u] = y[yy];
+    }
+#pragma unroll
+    for (int yy = 0; yy < 8; ++yy) {
+        int y[8];
+        idct8_aan(ws[yy][0], ws[yy][1], ws[yy][2], ws[yy][3], ws[yy][4], ws[yy][5], ws[yy][6], ws[yy][7],
+                  (1 << 14) + (128 << 15), y);
+        uint2 out;
+        out.x = pack_sat4(y[0] >> 15, y[1] >> 15, y[2] >> 15, y[3] >> 15);
+        out.y = pack_sat4(y[4] >> 15, y[5] >> 15, y[6] >> 15, y[7] >> 15);
+        *reinterpret_cast<uint2 *>(dst + yy * pitch) = out;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Colour conversion (Sec. 4.3, Alg. 2) in 16-bit fixed point with the
 // chroma offset and the rounding folded into one constant per channel:
 //   R = Y + ((91881 Cr - 11728000) >> 16)
