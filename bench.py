@@ -94,7 +94,7 @@ def measured_peaks():
 
 # Sources that decide the single-image launches' DRAM traffic: the device code
 # and the host code that plans those launches (strip widths, grids).
-TRAFFIC_SOURCES = ("jdec_api.cu", "jdec_common.h", "jdec_device.cuh", "jdec_kernels.cu", "jdec_launch.h",
+TRAFFIC_SOURCES = ("jdec_api.cu", "jdec_common.h", "jdec_device.cuh", "jdec_kernels.cu", "jdec_kernels.cuh", "jdec_launch.h",
                    "jdec_work.cuh")
 
 
@@ -311,12 +311,45 @@ def run_ours(args, ws, rank, local):
         out["serving"] = bench_serving(ctx, dev, [2000, 5000, 10000, 20000, 50000], args.serve_requests, 8.0)
     if not args.no_jpeg:
         out["jpeg"] = bench_jpeg(ctx, dev, stream)
+    if not args.no_aan:
+        out["idct_aan"] = bench_aan(ctx, stream, imgs, planes, rgbs, args.variants, per_var_ms,
+                                    min(K, args.aan_steps), keep)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(imgs, args.cpu_seconds)
     if ws > 1:
         torch.distributed.destroy_process_group()
     ctx.close()
     return out
+
+
+def bench_aan(ctx, stream, imgs, planes, rgbs, variants, llm_ms, steps, keep):
+    """The same step with the AAN scaled IDCT (JDEC_IDCT_AAN): per-variant
+    CUDA-event launch times beside the default LLM form's."""
+    import torch
+    from paper_1311_5304_gb300 import jdec
+    descs = [jdec.make_image(im.width, im.height, (im.h_samp, im.v_samp), planes[i], im.qtabs, rgbs[i],
+                             fancy=True, keep=keep, aan=True) for i, im in enumerate(imgs)]
+    for _ in range(5):
+        for d in descs:
+            ctx.decode_coeffs(d, stream)
+    ctx.sync(stream)
+    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in descs]
+           for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        for i, d in enumerate(descs):
+            evs[k][i][0].record(stream)
+            ctx.decode_coeffs(d, stream)
+            evs[k][i][1].record(stream)
+    torch.cuda.synchronize()
+    ctx.sync(stream)
+    ms = [statistics.mean(evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(steps)) for i in range(len(descs))]
+    px = sum(im.width * im.height for im in imgs)
+    return {"flag": "JDEC_IDCT_AAN", "steps": steps, "mpix_s": round(px / (sum(ms) / 1e3) / 1e6, 1),
+            "vs_llm": round(sum(llm_ms) / sum(ms), 4),
+            "by_variant": {v: {"ms": round(ms[i], 4), "llm_ms": round(llm_ms[i], 4),
+                               "gpix_s": round(imgs[i].width * imgs[i].height / (ms[i] / 1e3) / 1e9, 1)}
+                           for i, v in enumerate(variants)}}
 
 
 def bench_batched(ctx, dev, stream, steps, warmup, nimages=1024):
@@ -556,6 +589,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-jpeg", action="store_true", help="skip the whole-stream JPEG decode timing")
+    ap.add_argument("--no-aan", action="store_true", help="skip the AAN-IDCT timing of the step")
+    ap.add_argument("--aan-steps", type=int, default=300)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--batch-steps", type=int, default=6)
     ap.add_argument("--batch-images", type=int, default=1024)

@@ -67,6 +67,17 @@ typedef enum {
 #define JDEC_UPSAMPLE_FANCY     0u
 #define JDEC_UPSAMPLE_REPLICATE 1u
 
+/* IDCT selection (jdec_image.flags).  Default: the LLM-form integer IDCT
+ * (13-bit multipliers, 2 fractional bits between the passes).  JDEC_IDCT_AAN:
+ * the Arai-Agui-Nakajima scaled IDCT that Sec. 2 names -- the 2-D scale
+ * factors are folded into the dequantisation table (Q x round(2^12 s_v s_u),
+ * s_0 = 1, s_k = sqrt(2) cos(k pi/16)) and each 8-point pass takes five
+ * constant products, each an integer part plus the high word of a 32-bit
+ * fraction, with 12 fractional bits throughout and one rounding at the end.
+ * Both meet the IEEE 1180-1990 accuracy bounds; their samples differ by at
+ * most one level on ordinary content.  Each is bit-exact with its oracle. */
+#define JDEC_IDCT_AAN 2u
+
 /* Testing aid for failure detection (jdec_image.flags, jdec_decode_coeffs
  * only): the kernel arms its coefficient-load barriers but issues no loads,
  * so every CTA's bounded wait gives up after its limit (2 s), the CTA stops
@@ -100,7 +111,8 @@ typedef struct {
                                      read during the call, not retained         */
     uint8_t *rgb;                 /* DEVICE pointer to the RGB output          */
     int64_t rgb_pitch;            /* bytes per output row, >= 3*width          */
-    uint32_t flags;               /* JDEC_UPSAMPLE_* (| JDEC_TEST_*)           */
+    uint32_t flags;               /* JDEC_UPSAMPLE_* | JDEC_IDCT_AAN
+                                     (| JDEC_TEST_*)                            */
 } jdec_image;
 
 /* Creates a context on opt->device (default 0).  *out receives the context. */
@@ -165,7 +177,7 @@ JDEC_API jdec_status jdec_entropy_decode_mt(const uint8_t *data, size_t size, in
                                             int32_t threads);
 
 /* Decodes a baseline JPEG stream held in HOST memory into DEVICE RGB
- * (rgb_pitch >= 3*width; flags: JDEC_UPSAMPLE_*), overlapping host entropy
+ * (rgb_pitch >= 3*width; flags: JDEC_UPSAMPLE_* | JDEC_IDCT_AAN), overlapping host entropy
  * decoding with the device back-end (Sec. 4.5): the MCU rows are cut into
  * chunks; each decoded chunk is copied to context-owned device planes and
  * transformed while the host decodes the next ones.  With restart intervals

@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libjdec.so")
-SOURCES = ["jdec_api.cu", "jdec_runtime.cu", "jdec_batch.cu", "jdec_kernels.cu", "jdec_entropy.cpp", "jdec_noalloc.cu",
-           "jdec_pipeline.cu"]
+SOURCES = ["jdec_api.cu", "jdec_runtime.cu", "jdec_batch.cu", "jdec_kernels.cu", "jdec_kernels_batch.cu",
+           "jdec_entropy.cpp", "jdec_noalloc.cu", "jdec_pipeline.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

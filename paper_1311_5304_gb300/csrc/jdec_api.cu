@@ -6,6 +6,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -110,11 +111,12 @@ jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers, bool
     if (img->ncomp == 1) {
         // one component: 8x8 MCUs (T.81 A.2.2), output R = G = B = Y
         if (img->h_samp[0] != 1 || img->v_samp[0] != 1) return JDEC_EUNSUPPORTED;
-        if (img->flags & ~(JDEC_UPSAMPLE_REPLICATE | JDEC_TEST_WITHHOLD_LOADS)) return JDEC_EINVAL;
+        if (img->flags & ~(JDEC_UPSAMPLE_REPLICATE | JDEC_IDCT_AAN | JDEC_TEST_WITHHOLD_LOADS)) return JDEC_EINVAL;
         if ((img->flags & JDEC_TEST_WITHHOLD_LOADS) && !allow_test) return JDEC_EINVAL;
         g->hm = g->vm = 1;
         g->fancy = false;
         g->gray = true;
+        g->aan = (img->flags & JDEC_IDCT_AAN) != 0;
         g->W = img->width; g->H = img->height;
         g->mcus_x = (img->width + 7) / 8;
         g->mcus_y = (img->height + 7) / 8;
@@ -136,9 +138,10 @@ jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers, bool
         return JDEC_EUNSUPPORTED;
     const int hm = img->h_samp[0], vm = img->v_samp[0];
     if (hm > 2 || vm > 2) return JDEC_EUNSUPPORTED;   // 4:4:4, 4:2:2, 4:2:0, 4:4:0
-    if (img->flags & ~(JDEC_UPSAMPLE_REPLICATE | JDEC_TEST_WITHHOLD_LOADS)) return JDEC_EINVAL;
+    if (img->flags & ~(JDEC_UPSAMPLE_REPLICATE | JDEC_IDCT_AAN | JDEC_TEST_WITHHOLD_LOADS)) return JDEC_EINVAL;
     if ((img->flags & JDEC_TEST_WITHHOLD_LOADS) && !allow_test) return JDEC_EINVAL;
     g->hm = hm; g->vm = vm;
+    g->aan = (img->flags & JDEC_IDCT_AAN) != 0;
     g->fancy = (img->flags & JDEC_UPSAMPLE_REPLICATE) == 0 && (hm == 2 || vm == 2);
     g->W = img->width; g->H = img->height;
     g->mcus_x = (img->width + 8 * hm - 1) / (8 * hm);
@@ -212,6 +215,33 @@ void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int *
     *smem = L.total;
 }
 
+// AAN scale table S(v,u) = round(2^12 s_v s_u), s_0 = 1, s_k = sqrt(2) cos(k pi / 16)
+// ([8v + u]); the AAN transform's 2-D input scale folded into dequantisation.
+static const int32_t *aan_scale()
+{
+    static const struct Table {
+        int32_t s[64];
+        Table()
+        {
+            const double pi = 3.14159265358979323846;
+            double f[8];
+            for (int k = 0; k < 8; ++k) f[k] = k ? std::sqrt(2.0) * std::cos(k * pi / 16.0) : 1.0;
+            for (int v = 0; v < 8; ++v)
+                for (int u = 0; u < 8; ++u) s[8 * v + u] = static_cast<int32_t>(std::floor(4096.0 * f[v] * f[u] + 0.5));
+        }
+    } table;
+    return table.s;
+}
+
+int qmode_of(const jdec_image *img, const Geometry &g)
+{
+    if (g.aan) return kAAN;
+    for (int c = 0; c < (g.gray ? 1 : 3); ++c)
+        for (int k = 0; k < 64; ++k)
+            if (img->qtab[c][k] > 255) return kQ16;
+    return kQ8;
+}
+
 void fill_desc(ImageDesc *d, const jdec_image *img, const Geometry &g, int wt, int nctas)
 {
     memset(d, 0, sizeof(*d));
@@ -229,13 +259,12 @@ void fill_desc(ImageDesc *d, const jdec_image *img, const Geometry &g, int wt, i
     d->nidct = 32 * default_idct_warps(g.hm, g.vm);
     d->aligned8 = ((reinterpret_cast<uintptr_t>(img->rgb) | static_cast<uintptr_t>(img->rgb_pitch)) & 7) == 0;
     d->withhold = (img->flags & JDEC_TEST_WITHHOLD_LOADS) ? 1 : 0;
-    d->q8 = 1;
+    d->qmode = qmode_of(img, g);
+    const int32_t *S = aan_scale();
     for (int c = 0; c < 3; ++c) {
         const uint16_t *q = img->qtab[g.gray ? 0 : c];   // grayscale: the chroma blocks are zero
-        for (int k = 0; k < 64; ++k) {
-            d->q[c][k] = q[k];
-            if (q[k] > 255) d->q8 = 0;
-        }
+        // AAN: Q * S < 65536 * 2^13 fits int32
+        for (int k = 0; k < 64; ++k) d->q[c][k] = g.aan ? static_cast<int32_t>(q[k]) * S[k] : q[k];
     }
 }
 

@@ -161,11 +161,7 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
         int w = tuned_wt(ctx, g);
         wt[i] = std::max(1, std::min(w > 0 ? w : equal_strips(g.mcus_x, default_wt(g)), kMaxWT));
         var[i] = variant_of(g);
-        int q8 = 1;
-        for (int c = 0; c < (g.gray ? 1 : 3); ++c)
-            for (int k = 0; k < 64; ++k)
-                if (imgs[i].qtab[c][k] > 255) q8 = 0;
-        cls_of[i] = 2 * var[i] + q8;
+        cls_of[i] = kQModes * var[i] + qmode_of(&imgs[i], g);
         UnionLayout &u = U[cls_of[i]];
         // one variant per class launch: its own number of chroma slots
         u.nslot = default_slots(g.hm, g.vm, g.fancy);

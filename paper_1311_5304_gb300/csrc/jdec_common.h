@@ -15,10 +15,15 @@ constexpr int kMaxWT = 64;          // widest strip (MCUs) a launch accepts
 constexpr int kStages = 2;          // coefficient double buffer
 
 // Kernel variants (sampling x upsampling): 0: 4:4:4, 1/2: 4:2:2, 3/4: 4:2:0,
-// 5/6: 4:4:0 (replicate / triangular); a batch launch class is one variant
-// with or without the 8-bit dequantisation path: class = 2 * variant + q8.
+// 5/6: 4:4:0 (replicate / triangular).
 constexpr int kVariants = 7;
-constexpr int kClasses = 2 * kVariants;
+// Dequantisation + IDCT modes: the LLM form with 32-bit table entries, the
+// LLM form with 8-bit steps (dp2a dequantisation), the AAN scaled form
+// (prescaled 32-bit table).
+constexpr int kQ16 = 0, kQ8 = 1, kAAN = 2;
+constexpr int kQModes = 3;
+// A batch launch class is one variant in one mode: class = 3 * variant + mode.
+constexpr int kClasses = kQModes * kVariants;
 
 // Error codes a kernel writes to the context's device error word.
 constexpr int kErrTimeout = 1;      // an mbarrier wait gave up
@@ -35,12 +40,12 @@ struct ImageDesc {
     int32_t nstrips;
     int32_t nctas;          // CTAs sharing the strip-rows of this image
     int32_t aligned8;       // rgb and pitch are 8-byte aligned
-    int32_t q8;             // every quantisation step fits in 8 bits (dp2a path)
+    int32_t qmode;          // kQ16, kQ8 (every step fits in 8 bits) or kAAN
     int32_t row0, row1;     // MCU rows [row0, row1) covered by the launch
     int32_t nslot;          // chroma slots of the shared-memory ring (2 or 4)
     int32_t nidct;          // IDCT threads of the split roles (32, 64 or 96; unified roles: unused)
     int32_t withhold;       // testing aid: arm the load barriers, issue no loads
-    int32_t q[3][64];       // dequantisation tables, natural order
+    int32_t q[3][64];       // dequantisation tables, natural order (kAAN: prescaled)
 };
 
 // Region offsets shared by every variant decoded by one persistent launch:

@@ -158,8 +158,7 @@ jdec_status decode_batch_static(const jdec_image *imgs, int n, cudaStream_t s)
             double total = 0.0;
             for (int i = 0; i < n; ++i) {
                 const Geometry &g = t_geo[i];
-                const int q8 = hi[i].desc.q8 ? 1 : 0;
-                if (2 * hi[i].variant + q8 != cls) continue;
+                if (kQModes * hi[i].variant + hi[i].desc.qmode != cls) continue;
                 const int wt = hi[i].desc.wt;
                 const int ns = (g.mcus_x + wt - 1) / wt;
                 for (int stp = 0; stp < ns; ++stp)
@@ -172,8 +171,7 @@ jdec_status decode_batch_static(const jdec_image *imgs, int n, cudaStream_t s)
             double acc = 0.0;
             for (int i = 0; i < n; ++i) {
                 const Geometry &g = t_geo[i];
-                const int q8 = hi[i].desc.q8 ? 1 : 0;
-                if (2 * hi[i].variant + q8 != cls) continue;
+                if (kQModes * hi[i].variant + hi[i].desc.qmode != cls) continue;
                 const int wt = hi[i].desc.wt;
                 const int ns = (g.mcus_x + wt - 1) / wt;
                 for (int stp = 0; stp < ns; ++stp) {

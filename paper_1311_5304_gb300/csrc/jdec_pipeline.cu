@@ -229,7 +229,7 @@ extern "C" JDEC_API jdec_status jdec_decode_jpeg(jdec_ctx *ctx, const uint8_t *d
                                                  int64_t rgb_pitch, uint32_t flags, int32_t threads, void *stream)
 {
     if (!ctx || !data || !rgb) return JDEC_EINVAL;
-    if (flags & ~JDEC_UPSAMPLE_REPLICATE) return JDEC_EINVAL;
+    if (flags & ~(JDEC_UPSAMPLE_REPLICATE | JDEC_IDCT_AAN)) return JDEC_EINVAL;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return JDEC_ECUDA;
     if (dev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return JDEC_ECUDA;

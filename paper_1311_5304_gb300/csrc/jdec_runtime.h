@@ -16,6 +16,7 @@ struct Geometry {
     int hm, vm;
     bool fancy;
     bool gray;       // one component: decoded as 4:4:4 with all-zero chroma blocks
+    bool aan;        // AAN scaled IDCT instead of the LLM form
     int W, H;
     int mcus_x, mcus_y;
     int cw, ch;
@@ -77,6 +78,9 @@ bool encode_plane_map(CUtensorMap *m, const int16_t *base, int bw, int bh, int b
 jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers, bool allow_test = false);
 void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int *wt, int *nctas, int *smem);
 void fill_desc(ImageDesc *d, const jdec_image *img, const Geometry &g, int wt, int nctas);
+// Dequantisation + IDCT mode of an image: kAAN when asked for, else kQ8 when
+// every quantisation step fits in 8 bits, else kQ16.
+int qmode_of(const jdec_image *img, const Geometry &g);
 bool encode_maps(CUtensorMap maps[3], const jdec_image *img, const Geometry &g, int wt);
 // Device address (current device) of a small all-zero coefficient plane that
 // stands in for the chroma planes of a grayscale image (null on failure).

@@ -267,22 +267,22 @@ __device__ __forceinline__ void fix_edges(uint8_t *slot, int lc, int mx0, int cw
 // this image's dequantisation tables first.
 // Writes the dequantisation tables of `d` into shared memory in the layout the
 // IDCT expects (packed bytes for dp2a, or transposed int32).
-template <bool Q8>
+template <int QM>
 __device__ __forceinline__ void load_qtables(int *qs, const ImageDesc &d, int tid, int nthreads)
 {
-    if (Q8) {
+    if (QM == kQ8) {
         // word 64*c + 8*pr + v = Q_c(v, 2pr) | Q_c(v, 2pr+1) << 24
         for (int i = tid; i < 96; i += nthreads) {
             const int c = i >> 5, pr = (i >> 3) & 3, v = i & 7;
             qs[64 * c + 8 * pr + v] = d.q[c][8 * v + 2 * pr] | (d.q[c][8 * v + 2 * pr + 1] << 24);
         }
     } else {
-        // qs[64*c + 8*u + v] = Q_c(v, u)
+        // qs[64*c + 8*u + v] = Q_c(v, u) (prescaled for the AAN transform)
         for (int i = tid; i < 192; i += nthreads) qs[i] = d.q[i >> 6][((i & 7) << 3) | ((i >> 3) & 7)];
     }
 }
 
-template <int HM, int VM, bool FANCY, bool Q8>
+template <int HM, int VM, bool FANCY, int QM>
 __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const ImageDesc &qsrc, int strip, int r0,
                                int r1, uint8_t *smem, const SmemLayout &L, PipeState &ps, int *err, bool last,
                                bool reload_q)
@@ -308,7 +308,7 @@ __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const Im
         int *qs = reinterpret_cast<int *>(smem + L.off_q);
         if (reload_q) {
             // every IDCT thread is past its last use of the previous tables
-            load_qtables<Q8>(qs, qsrc, tid, nidct);
+            load_qtables<QM>(qs, qsrc, tid, nidct);
             named_sync(kBarIdct, nidct);
         }
         const int lb0 = (V::kHalo && mx0 == 0) ? 1 : 0;
@@ -363,8 +363,10 @@ __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const Im
                     dst = slot + comp * 8 * L.lc + 8 * lb;
                     pitch = L.lc;
                 }
-                if (Q8)
+                if (QM == kQ8)
                     idct_block_q8(blk, reinterpret_cast<const uint32_t *>(q), dst, pitch);
+                else if (QM == kAAN)
+                    idct_block_aan(blk, q, dst, pitch);
                 else
                     idct_block(blk, q, dst, pitch);
             }
@@ -447,7 +449,7 @@ __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const Im
 // the barrier of job k+1, which every thread reaches only after finishing the
 // colour tasks of job k.  No named barrier is left half-signalled, so an item
 // of either kind may follow.
-template <int HM, int VM, bool FANCY, bool Q8>
+template <int HM, int VM, bool FANCY, int QM>
 __device__ bool run_work_unified(const CUtensorMap *tm, const ItemDesc d, const ImageDesc &qsrc, int strip, int r0,
                                  int r1, uint8_t *smem, const SmemLayout &L, PipeState &ps, int *err, bool reload_q)
 {
@@ -469,7 +471,7 @@ __device__ bool run_work_unified(const CUtensorMap *tm, const ItemDesc d, const 
     if (reload_q) {
         // every thread is past the barrier that follows the previous item's
         // last IDCT tasks, so nobody reads the old tables any more
-        load_qtables<Q8>(qs, qsrc, tid, kCtaThreads);
+        load_qtables<QM>(qs, qsrc, tid, kCtaThreads);
         __syncthreads();
     }
     const int lb0 = (V::kHalo && mx0 == 0) ? 1 : 0;
@@ -531,8 +533,10 @@ __device__ bool run_work_unified(const CUtensorMap *tm, const ItemDesc d, const 
                 dst = slot + comp * 8 * L.lc + 8 * lb;
                 pitch = L.lc;
             }
-            if (Q8)
+            if (QM == kQ8)
                 idct_block_q8(blk, reinterpret_cast<const uint32_t *>(q), dst, pitch);
+            else if (QM == kAAN)
+                idct_block_aan(blk, q, dst, pitch);
             else
                 idct_block(blk, q, dst, pitch);
         }
@@ -580,14 +584,14 @@ __device__ bool run_work_unified(const CUtensorMap *tm, const ItemDesc d, const 
 // split roles (see run_work_split and run_work_unified).  `last` = this is
 // the CTA's final item, or the next item may use the other kind of roles:
 // the split version then drains its barriers.
-template <int HM, int VM, bool FANCY, bool Q8, bool UNI>
+template <int HM, int VM, bool FANCY, int QM, bool UNI>
 __device__ __forceinline__ bool run_work(const CUtensorMap *tm, const ItemDesc d, const ImageDesc &qsrc, int strip,
                                          int r0, int r1, uint8_t *smem, const SmemLayout &L, PipeState &ps, int *err,
                                          bool last, bool reload_q)
 {
     if (UNI && Variant<HM, VM, FANCY>::kCanUnify)
-        return run_work_unified<HM, VM, FANCY, Q8>(tm, d, qsrc, strip, r0, r1, smem, L, ps, err, reload_q);
-    return run_work_split<HM, VM, FANCY, Q8>(tm, d, qsrc, strip, r0, r1, smem, L, ps, err, last, reload_q);
+        return run_work_unified<HM, VM, FANCY, QM>(tm, d, qsrc, strip, r0, r1, smem, L, ps, err, reload_q);
+    return run_work_split<HM, VM, FANCY, QM>(tm, d, qsrc, strip, r0, r1, smem, L, ps, err, last, reload_q);
 }
 
 }  // namespace jdec
@@ -597,7 +601,7 @@ namespace jdec {
 // Runs this CTA's share of an image: the strips' MCU rows in [row0, row1),
 // concatenated strip after strip, split evenly over `nctas` CTAs; `b` is the
 // CTA's index among them.
-template <int HM, int VM, bool FANCY, bool Q8, bool UNI>
+template <int HM, int VM, bool FANCY, int QM, bool UNI>
 __device__ bool run_share(const CUtensorMap *tm, const ImageDesc &d, int b, uint8_t *smem, const SmemLayout &L,
                           PipeState &ps, int *err, bool last_image)
 {
@@ -611,7 +615,7 @@ __device__ bool run_share(const CUtensorMap *tm, const ImageDesc &d, int b, uint
         const int rr = static_cast<int>(a - s * nrows);
         const int len = static_cast<int>(min(e - a, nrows - rr));
         a += len;
-        if (!run_work<HM, VM, FANCY, Q8, UNI>(tm, id, d, s, d.row0 + rr, d.row0 + rr + len, smem, L, ps, err,
+        if (!run_work<HM, VM, FANCY, QM, UNI>(tm, id, d, s, d.row0 + rr, d.row0 + rr + len, smem, L, ps, err,
                                          last_image && a >= e, false))
             return false;
     }

@@ -20,6 +20,7 @@ _lib = None
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, EBUSY, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 UPSAMPLE_FANCY, UPSAMPLE_REPLICATE = 0, 1
+IDCT_AAN = 2   # the AAN scaled IDCT instead of the default LLM form
 TEST_WITHHOLD_LOADS = 0x80000000   # testing aid: the kernel's bounded waits run out (JDEC_ETIMEOUT)
 SAMPLINGS = {"444": ((1, 1, 1), (1, 1, 1)), "422": ((2, 1, 1), (1, 1, 1)), "420": ((2, 1, 1), (2, 1, 1)),
              "440": ((1, 1, 1), (2, 1, 1))}
@@ -162,12 +163,17 @@ def _stream_ptr(stream) -> int:
     return stream.cuda_stream
 
 
+def _flags(fancy, aan):
+    return (UPSAMPLE_FANCY if fancy else UPSAMPLE_REPLICATE) | (IDCT_AAN if aan else 0)
+
+
 def make_image(width, height, sampling, planes, qtabs, rgb, rgb_pitch=None, fancy=True,
-               keep=None, host=False) -> Image:
+               keep=None, host=False, aan=False) -> Image:
     """Fills a ``jdec_image``.  planes: 3 int16 arrays/tensors shaped
     (blocks_h, blocks_w, 64), or 1 for a grayscale image (sampling "gray");
     qtabs: one host uint16 array of 64 per plane; rgb: uint8 buffer (device
-    tensor, or host numpy array with ``host=True``)."""
+    tensor, or host numpy array with ``host=True``); ``aan`` selects the AAN
+    IDCT."""
     ncomp = len(planes)
     hs, vs = ((1, 1, 1), (1, 1, 1)) if ncomp == 1 else (SAMPLINGS[sampling] if isinstance(sampling, str) else sampling)
     im = Image()
@@ -195,12 +201,12 @@ def make_image(width, height, sampling, planes, qtabs, rgb, rgb_pitch=None, fanc
         im.rgb = rgb.data_ptr()
         im.rgb_pitch = int(rgb_pitch if rgb_pitch is not None else rgb.stride(0))
     keep.append(rgb)
-    im.flags = UPSAMPLE_FANCY if fancy else UPSAMPLE_REPLICATE
+    im.flags = _flags(fancy, aan)
     return im
 
 
 def make_image_flat(width, height, sampling, base_ptr: int, shapes, qtabs, rgb_ptr: int, rgb_pitch: int,
-                    fancy=True, keep=None) -> Image:
+                    fancy=True, keep=None, aan=False) -> Image:
     """Fills a ``jdec_image`` whose planes lie one after another in one device
     buffer starting at ``base_ptr`` (shapes: (blocks_h, blocks_w) per plane;
     3 planes, or 1 for grayscale); ``rgb_ptr``: device RGB buffer."""
@@ -222,7 +228,7 @@ def make_image_flat(width, height, sampling, base_ptr: int, shapes, qtabs, rgb_p
         im.qtab[c] = q.ctypes.data
     im.rgb = int(rgb_ptr)
     im.rgb_pitch = int(rgb_pitch)
-    im.flags = UPSAMPLE_FANCY if fancy else UPSAMPLE_REPLICATE
+    im.flags = _flags(fancy, aan)
     return im
 
 
@@ -275,12 +281,12 @@ class Context:
         return st
 
     def decode_jpeg(self, data: bytes, rgb, fancy: bool = True, threads: int = 1, stream=None,
-                    check=True) -> int:
+                    check=True, aan: bool = False) -> int:
         """Baseline JPEG bytes (host) -> device RGB tensor (H, W, 3) or (H, pitch)
         uint8; host entropy decoding overlaps the device back-end."""
         buf = bytes(data)
         st = self._lib.jdec_decode_jpeg(self._h, ctypes.c_char_p(buf), len(buf), ctypes.c_void_p(rgb.data_ptr()),
-                                        int(rgb.stride(0)), UPSAMPLE_FANCY if fancy else UPSAMPLE_REPLICATE,
+                                        int(rgb.stride(0)), _flags(fancy, aan),
                                         int(threads), ctypes.c_void_p(_stream_ptr(stream)))
         if check and st != OK:
             raise JdecError(st, "jdec_decode_jpeg")
@@ -299,9 +305,10 @@ class Context:
         return st
 
 
-def decode(ctx: Context, img, device_planes=None, rgb=None, stream=None):
+def decode(ctx: Context, img, device_planes=None, rgb=None, stream=None, aan=False):
     """Convenience: decode a ``synth.CoefImage`` whose planes are uploaded to
-    the current CUDA device; returns the (H, W, 3) uint8 device tensor."""
+    the current CUDA device; returns the (H, W, 3) uint8 device tensor
+    (``aan``: with the AAN IDCT)."""
     import torch
     if device_planes is None:
         device_planes = [torch.from_numpy(np.ascontiguousarray(p)).cuda() for p in img.planes]
@@ -309,6 +316,6 @@ def decode(ctx: Context, img, device_planes=None, rgb=None, stream=None):
         rgb = torch.empty((img.height, img.width, 3), dtype=torch.uint8, device="cuda")
     keep = []
     im = make_image(img.width, img.height, (img.h_samp, img.v_samp), device_planes, img.qtabs, rgb,
-                    fancy=img.fancy, keep=keep)
+                    fancy=img.fancy, keep=keep, aan=aan)
     ctx.decode_coeffs(im, stream)
     return rgb

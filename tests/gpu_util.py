@@ -9,10 +9,10 @@ from paper_1311_5304_gb300 import jdec, synth
 POISON = 0xCD
 
 
-def oracle_rgb(orc, img, threads=None):
+def oracle_rgb(orc, img, threads=None, aan=False):
     threads = threads or max(1, min(32, os.cpu_count() or 1))
     return orc.backend_decode(img.width, img.height, img.h_samp, img.v_samp, img.planes, img.qtabs,
-                              img.fancy, threads=threads)
+                              img.fancy, threads=threads, aan=aan)
 
 
 def upload(img):
@@ -20,7 +20,7 @@ def upload(img):
     return [torch.from_numpy(np.ascontiguousarray(p)).cuda() for p in img.planes]
 
 
-def gpu_rgb(ctx, img, pitch=None, offset=0, planes=None, check=True):
+def gpu_rgb(ctx, img, pitch=None, offset=0, planes=None, check=True, aan=False):
     """Decodes on the GPU into a poisoned buffer; returns (rgb HxWx3, raw
     buffer as numpy) so callers can check the untouched bytes too."""
     import torch
@@ -30,7 +30,7 @@ def gpu_rgb(ctx, img, pitch=None, offset=0, planes=None, check=True):
     view = raw[offset:]
     keep = []
     im = jdec.make_image(img.width, img.height, (img.h_samp, img.v_samp), planes, img.qtabs, view,
-                         rgb_pitch=pitch, fancy=img.fancy, keep=keep)
+                         rgb_pitch=pitch, fancy=img.fancy, keep=keep, aan=aan)
     st = ctx.decode_coeffs(im, check=check)
     torch.cuda.synchronize()
     if check:

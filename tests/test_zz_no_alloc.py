@@ -32,7 +32,7 @@ def _descs(imgs, planes, keep):
     import torch
     rgbs = [torch.full((im.height, im.width, 3), 0xCD, dtype=torch.uint8, device="cuda") for im in imgs]
     ds = [jdec.make_image(im.width, im.height, (im.h_samp, im.v_samp), planes[i], im.qtabs, rgbs[i],
-                          fancy=im.fancy, keep=keep) for i, im in enumerate(imgs)]
+                          fancy=im.fancy, keep=keep, aan=(i % 3 == 0)) for i, im in enumerate(imgs)]
     return ds, rgbs
 
 
