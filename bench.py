@@ -10,7 +10,7 @@ step, far larger than L2, so no flush is needed between steps.
 
   value       MPix/s over the timed steps (device-timed, CUDA events), summed
               over ranks (each rank decodes its own replica: weak scaling)
-  e2e         the same metric through jdec_decode_host: pinned host planes in,
+  e2e         the same metric through jdec_decode_host_batch: pinned host planes in,
               pinned host RGB out, copies inside the timed region
   roofline    algorithmic bytes (128 B per coefficient block + 3 B per pixel)
               per launch / mean launch time, against the measured HBM peak
@@ -248,8 +248,7 @@ def run_ours(args, ws, rank, local):
         hdescs = [jdec.make_image(im.width, im.height, (im.h_samp, im.v_samp),
                                   [hp.numpy() for hp in host_planes[i]], im.qtabs, host_rgb[i].numpy(),
                                   fancy=True, keep=keep, host=True) for i, im in enumerate(imgs)]
-        for d in hdescs:
-            ctx.decode_host(d, stream)
+        ctx.decode_host_batch(hdescs, stream)
         ctx.sync(stream)
         Ke = max(1, min(args.e2e_steps, K))
         if ws > 1:
@@ -258,8 +257,7 @@ def run_ours(args, ws, rank, local):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(Ke):
-            for d in hdescs:
-                ctx.decode_host(d, stream)
+            ctx.decode_host_batch(hdescs, stream)
         b.record(stream)
         torch.cuda.synchronize(dev)
         if ws > 1:
@@ -270,7 +268,8 @@ def run_ours(args, ws, rank, local):
                "h2d_bytes_per_step": int(sum(im.coef_bytes() for im in imgs)),
                "d2h_bytes_per_step": int(sum(im.rgb_bytes() for im in imgs)),
                "steps": Ke, "ms_per_step": round(e_ms / Ke, 3),
-               "api": "jdec_decode_host (pinned host buffers, banded H2D/decode/D2H)"}
+               "api": "jdec_decode_host_batch (the step's images from pinned host buffers; banded "
+                      "H2D/decode/D2H overlapping across images)"}
 
     peaks, peak_kind = measured_peaks()
     peak = float(peaks["hbm_gbs"])
@@ -311,6 +310,10 @@ def run_ours(args, ws, rank, local):
         out["serving"] = bench_serving(ctx, dev, [2000, 5000, 10000, 20000, 50000], args.serve_requests, 8.0)
     if not args.no_jpeg:
         out["jpeg"] = bench_jpeg(ctx, dev, stream)
+    if not args.no_sparsity:
+        out["sparsity"] = bench_sparsity(ctx, dev, stream)
+        for r in out["sparsity"]["by_quality"]:
+            r["frac"] = round(r["gbs"] / float(measured_peaks()[0]["hbm_gbs"]), 4)
     if not args.no_aan:
         out["idct_aan"] = bench_aan(ctx, stream, imgs, planes, rgbs, args.variants, per_var_ms,
                                     min(K, args.aan_steps), keep)
@@ -320,6 +323,54 @@ def run_ours(args, ws, rank, local):
         torch.distributed.destroy_process_group()
     ctx.close()
     return out
+
+
+CONFIG3 = [(30, 2), (50, 4), (75, 8), (90, 16), (98, 32)]   # (quality, grain sigma)
+
+
+def bench_sparsity(ctx, dev, stream, reps=20):
+    """4000x3000 4:2:0 images across the quality / detail sweep (triangular
+    upsampling).  One image is 72 MB of traffic, below L2's 129 MB, so each
+    quality is timed over rotating copies in separate buffers totalling at
+    least 4 x L2."""
+    import torch
+    from paper_1311_5304_gb300 import jdec, synth
+    out = []
+    for q, sigma in CONFIG3:
+        img = synth.make_image(4000, 3000, "420", q, seed=13115304 + 3000 + q, kind="gradient", sigma=sigma,
+                               fancy=True)
+        nbytes = alg_bytes(img)
+        nsets = -(-4 * L2_BYTES // nbytes)
+        keep = []
+        descs = []
+        for _ in range(nsets):
+            pl = [torch.from_numpy(np.ascontiguousarray(p)).to(dev) for p in img.planes]
+            rgb = torch.empty((img.height, img.width, 3), dtype=torch.uint8, device=dev)
+            descs.append(jdec.make_image(img.width, img.height, "420", pl, img.qtabs, rgb, fancy=True, keep=keep))
+        for d in descs:
+            ctx.decode_coeffs(d, stream)
+        ctx.sync(stream)
+        evs = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(reps * nsets)]
+        torch.cuda.synchronize(dev)
+        for r in range(reps):
+            for i, d in enumerate(descs):
+                e = evs[r * nsets + i]
+                e[0].record(stream)
+                ctx.decode_coeffs(d, stream)
+                e[1].record(stream)
+        torch.cuda.synchronize(dev)
+        ctx.sync(stream)
+        t = sorted(a.elapsed_time(b) for a, b in evs)
+        ms = statistics.mean(t)
+        bits = 8.0 * len(synth.encode_jfif(img)) / (img.width * img.height)
+        out.append({"quality": q, "sigma": sigma, "nonzero_ac": round(synth.nonzero_ac_fraction(img), 4),
+                    "bits_per_px": round(bits, 3), "us": round(ms * 1e3, 2), "us_p99": round(t[(99 * len(t)) // 100] * 1e3, 2),
+                    "gpix_s": round(img.width * img.height / (ms / 1e3) / 1e9, 1),
+                    "gbs": round(nbytes / (ms / 1e3) / 1e9, 1)})
+        del descs, keep
+    return {"workload": "4000x3000 4:2:0, gradient + grain, q30..98, triangular upsampling",
+            "l2": "rotating copies in separate buffers, >= 4 x L2 per quality", "launches_per_quality": "reps x copies",
+            "by_quality": out}
 
 
 def bench_aan(ctx, stream, imgs, planes, rgbs, variants, llm_ms, steps, keep):
@@ -590,6 +641,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-jpeg", action="store_true", help="skip the whole-stream JPEG decode timing")
     ap.add_argument("--no-aan", action="store_true", help="skip the AAN-IDCT timing of the step")
+    ap.add_argument("--no-sparsity", action="store_true", help="skip the 4000x3000 quality sweep")
     ap.add_argument("--aan-steps", type=int, default=300)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--batch-steps", type=int, default=6)

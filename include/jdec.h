@@ -138,6 +138,16 @@ JDEC_API jdec_status jdec_decode_batch(jdec_ctx *ctx, const jdec_image *imgs, in
  * valid until the stream has executed the copies. */
 JDEC_API jdec_status jdec_decode_host(jdec_ctx *ctx, const jdec_image *img, void *stream);
 
+/* jdec_decode_host for n images in one call: the images are decoded in order,
+ * and the copies and decoding of consecutive images overlap (the library
+ * stages them in two alternating sets of device buffers it owns, sized for
+ * the largest two images).  Stream-ordered on `stream` as a whole: the call
+ * starts after earlier work on the stream, and later work waits for the last
+ * copy back.  Every description is validated before anything is enqueued
+ * (first invalid one -> its status, nothing launched).  Results are identical
+ * to n jdec_decode_host calls. */
+JDEC_API jdec_status jdec_decode_host_batch(jdec_ctx *ctx, const jdec_image *imgs, int32_t n, void *stream);
+
 /* Synchronises `stream` and reports any device-side error recorded by earlier
  * launches of this context (a bounded wait that gave up -> JDEC_ETIMEOUT).
  * Clears the recorded error. */

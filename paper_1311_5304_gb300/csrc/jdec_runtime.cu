@@ -172,37 +172,46 @@ static cudaEvent_t band_event(jdec_ctx *ctx, int i)
     return i < ctx->n_band_ev ? ctx->band_ev[i] : nullptr;
 }
 
-jdec_status decode_host_banded(jdec_ctx *ctx, const jdec_image *himg, const Geometry &g, cudaStream_t s)
+// Event indices of the host-buffer calls: per staging slot b, [16b, 16b + nb)
+// after the H2D of band k, [16b + 8, 16b + 8 + nb) after its decode; then the
+// fork and join of the call and, per slot, "decode done" and "copy-back done".
+constexpr int kBands = 8;
+constexpr int kEvFork = 32, kEvJoin = 33, kEvCompDone = 34, kEvD2hDone = 36;
+
+// Enqueues one image's banded H2D / decode / D2H on the three host streams,
+// staged in slot b.  The slot's previous image (two images earlier in the
+// same call, or an earlier call) must have finished decoding before its
+// planes are overwritten, and finished copying back before its RGB is.
+static jdec_status host_image(jdec_ctx *ctx, const jdec_image *himg, const Geometry &g, int b, HostStreams &hs)
 {
-    // device staging: three planes (256-byte aligned) + dense RGB
+    // device staging: the planes (256-byte aligned) + dense RGB
     const int ncomp = g.gray ? 1 : 3;
     size_t off[3] = {0, 0, 0}, tot = 0;
     for (int c = 0; c < ncomp; ++c) {
         off[c] = tot;
         tot += (static_cast<size_t>(himg->blocks_w[c]) * himg->blocks_h[c] * 128 + 255) & ~static_cast<size_t>(255);
     }
-    jdec_status st = ensure_buffer(ctx, &ctx->h_coef, &ctx->h_coef_cap, tot);
+    jdec_status st = ensure_buffer(ctx, &ctx->h_coef[b], &ctx->h_coef_cap[b], tot);
     if (st != JDEC_OK) return st;
     const size_t rgb_pitch = 3 * static_cast<size_t>(g.W);
-    st = ensure_buffer(ctx, &ctx->h_rgb, &ctx->h_rgb_cap, rgb_pitch * g.H);
+    st = ensure_buffer(ctx, &ctx->h_rgb[b], &ctx->h_rgb_cap[b], rgb_pitch * g.H);
     if (st != JDEC_OK) return st;
 
     jdec_image dimg = *himg;
     for (int c = 0; c < ncomp; ++c)
-        dimg.coef[c] = reinterpret_cast<const int16_t *>(static_cast<uint8_t *>(ctx->h_coef) + off[c]);
-    dimg.rgb = static_cast<uint8_t *>(ctx->h_rgb);
+        dimg.coef[c] = reinterpret_cast<const int16_t *>(static_cast<uint8_t *>(ctx->h_coef[b]) + off[c]);
+    dimg.rgb = static_cast<uint8_t *>(ctx->h_rgb[b]);
     dimg.rgb_pitch = static_cast<int64_t>(rgb_pitch);
 
-    HostStreams &hs = host_streams(ctx);
-    const int nb = std::min(8, g.mcus_y);
-    // bands: event indices [0, nb) after H2D of band k, [nb, 2nb) after decode
-    cudaEvent_t fork = band_event(ctx, 2 * nb);
-    cudaEvent_t join = band_event(ctx, 2 * nb + 1);
-    if (!fork || !join) return JDEC_ECUDA;
-    if (cudaEventRecord(fork, s) != cudaSuccess) return JDEC_ECUDA;
-    cudaStreamWaitEvent(hs.h2d, fork, 0);
-    cudaStreamWaitEvent(hs.comp, fork, 0);
-    cudaStreamWaitEvent(hs.d2h, fork, 0);
+    const int nb = std::min(kBands, g.mcus_y);
+    const int e0 = 16 * b;
+    cudaEvent_t comp_done = band_event(ctx, kEvCompDone + b), d2h_done = band_event(ctx, kEvD2hDone + b);
+    for (int i = 0; i < 2 * kBands; ++i)
+        if (!band_event(ctx, e0 + i)) return JDEC_ECUDA;
+    if (!comp_done || !d2h_done) return JDEC_ECUDA;
+    // (waits on an event never recorded return at once)
+    if (cudaStreamWaitEvent(hs.h2d, comp_done, 0) != cudaSuccess) return JDEC_ECUDA;
+    if (cudaStreamWaitEvent(hs.comp, d2h_done, 0) != cudaSuccess) return JDEC_ECUDA;
     const int lookahead = (g.fancy && g.vm == 2) ? 1 : 0;
     for (int k = 0; k < nb; ++k) {
         const int r0 = static_cast<int>(static_cast<long>(g.mcus_y) * k / nb);
@@ -212,21 +221,21 @@ jdec_status decode_host_banded(jdec_ctx *ctx, const jdec_image *himg, const Geom
             const size_t row_bytes = static_cast<size_t>(himg->blocks_w[c]) * 128;
             const size_t o = static_cast<size_t>(r0) * v * row_bytes;
             const size_t n = static_cast<size_t>(r1 - r0) * v * row_bytes;
-            if (cudaMemcpyAsync(static_cast<uint8_t *>(ctx->h_coef) + off[c] + o,
+            if (cudaMemcpyAsync(static_cast<uint8_t *>(ctx->h_coef[b]) + off[c] + o,
                                 reinterpret_cast<const uint8_t *>(himg->coef[c]) + o, n, cudaMemcpyHostToDevice,
                                 hs.h2d) != cudaSuccess)
                 return JDEC_ECUDA;
         }
-        cudaEventRecord(band_event(ctx, k), hs.h2d);
+        if (cudaEventRecord(band_event(ctx, e0 + k), hs.h2d) != cudaSuccess) return JDEC_ECUDA;
         // decode band k - lookahead once its chroma look-ahead row has arrived
         const int kd = k - lookahead;
         if (kd >= 0) {
-            cudaStreamWaitEvent(hs.comp, band_event(ctx, k), 0);
+            if (cudaStreamWaitEvent(hs.comp, band_event(ctx, e0 + k), 0) != cudaSuccess) return JDEC_ECUDA;
             const int d0 = static_cast<int>(static_cast<long>(g.mcus_y) * kd / nb);
             const int d1 = static_cast<int>(static_cast<long>(g.mcus_y) * (kd + 1) / nb);
             st = launch_rows(ctx, &dimg, g, hs.comp, d0, d1, 0);
             if (st != JDEC_OK) return st;
-            cudaEventRecord(band_event(ctx, nb + kd), hs.comp);
+            if (cudaEventRecord(band_event(ctx, e0 + kBands + kd), hs.comp) != cudaSuccess) return JDEC_ECUDA;
         }
     }
     if (lookahead) {
@@ -234,30 +243,59 @@ jdec_status decode_host_banded(jdec_ctx *ctx, const jdec_image *himg, const Geom
         const int d0 = static_cast<int>(static_cast<long>(g.mcus_y) * kd / nb);
         st = launch_rows(ctx, &dimg, g, hs.comp, d0, g.mcus_y, 0);
         if (st != JDEC_OK) return st;
-        cudaEventRecord(band_event(ctx, nb + kd), hs.comp);
+        if (cudaEventRecord(band_event(ctx, e0 + kBands + kd), hs.comp) != cudaSuccess) return JDEC_ECUDA;
     }
+    if (cudaEventRecord(comp_done, hs.comp) != cudaSuccess) return JDEC_ECUDA;
     const int mcu_h = 8 * g.vm;
     for (int k = 0; k < nb; ++k) {
         const int r0 = static_cast<int>(static_cast<long>(g.mcus_y) * k / nb);
         const int r1 = static_cast<int>(static_cast<long>(g.mcus_y) * (k + 1) / nb);
         const int y0 = r0 * mcu_h, y1 = std::min(g.H, r1 * mcu_h);
         if (y1 <= y0) continue;
-        cudaStreamWaitEvent(hs.d2h, band_event(ctx, nb + k), 0);
+        if (cudaStreamWaitEvent(hs.d2h, band_event(ctx, e0 + kBands + k), 0) != cudaSuccess) return JDEC_ECUDA;
         if (cudaMemcpy2DAsync(himg->rgb + static_cast<int64_t>(y0) * himg->rgb_pitch, himg->rgb_pitch,
-                              static_cast<uint8_t *>(ctx->h_rgb) + y0 * rgb_pitch, rgb_pitch, rgb_pitch, y1 - y0,
+                              static_cast<uint8_t *>(ctx->h_rgb[b]) + y0 * rgb_pitch, rgb_pitch, rgb_pitch, y1 - y0,
                               cudaMemcpyDeviceToHost, hs.d2h) != cudaSuccess)
             return JDEC_ECUDA;
     }
+    if (cudaEventRecord(d2h_done, hs.d2h) != cudaSuccess) return JDEC_ECUDA;
+    return JDEC_OK;
+}
+
+jdec_status decode_host_many(jdec_ctx *ctx, const jdec_image *imgs, const Geometry *geo, int n, cudaStream_t s)
+{
+    HostStreams &hs = host_streams(ctx);
+    cudaEvent_t fork = band_event(ctx, kEvFork);
+    cudaEvent_t join = band_event(ctx, kEvJoin);
+    if (!fork || !join) return JDEC_ECUDA;
+    // everything earlier on s happens first ...
+    if (cudaEventRecord(fork, s) != cudaSuccess) return JDEC_ECUDA;
+    cudaStreamWaitEvent(hs.h2d, fork, 0);
+    cudaStreamWaitEvent(hs.comp, fork, 0);
+    cudaStreamWaitEvent(hs.d2h, fork, 0);
+    jdec_status st = JDEC_OK;
+    for (int i = 0; i < n && st == JDEC_OK; ++i) st = host_image(ctx, &imgs[i], geo[i], i & 1, hs);
+    // ... and everything later on s waits for the last copy back (also when
+    // an image failed to enqueue: what was enqueued still completes first)
     if (cudaEventRecord(join, hs.d2h) != cudaSuccess) return JDEC_ECUDA;
     if (cudaStreamWaitEvent(s, join, 0) != cudaSuccess) return JDEC_ECUDA;
-    return JDEC_OK;
+    return st;
+}
+
+jdec_status decode_host_banded(jdec_ctx *ctx, const jdec_image *himg, const Geometry &g, cudaStream_t s)
+{
+    return decode_host_many(ctx, himg, &g, 1, s);
 }
 
 void release_runtime(jdec_ctx *ctx)
 {
-    if (ctx->h_coef) cudaFree(ctx->h_coef);
-    if (ctx->h_rgb) cudaFree(ctx->h_rgb);
-    ctx->h_coef = ctx->h_rgb = nullptr;
+    for (int b = 0; b < 2; ++b) {
+        if (ctx->h_coef[b]) cudaFree(ctx->h_coef[b]);
+        if (ctx->h_rgb[b]) cudaFree(ctx->h_rgb[b]);
+        ctx->h_coef[b] = ctx->h_rgb[b] = nullptr;
+        ctx->owned_bytes -= ctx->h_coef_cap[b] + ctx->h_rgb_cap[b];
+        ctx->h_coef_cap[b] = ctx->h_rgb_cap[b] = 0;
+    }
     for (int i = 0; i < ctx->n_band_ev; ++i) cudaEventDestroy(ctx->band_ev[i]);
     ctx->n_band_ev = 0;
     release_batch(ctx);
@@ -265,3 +303,20 @@ void release_runtime(jdec_ctx *ctx)
 }
 
 }  // namespace jdec
+
+extern "C" JDEC_API jdec_status jdec_decode_host_batch(jdec_ctx *ctx, const jdec_image *imgs, int32_t n, void *stream)
+{
+    if (!ctx || n < 0 || (n > 0 && !imgs)) return JDEC_EINVAL;
+    if (n == 0) return JDEC_OK;
+    std::vector<jdec::Geometry> geo(static_cast<size_t>(n));
+    for (int i = 0; i < n; ++i) {
+        const jdec_status st = jdec::validate(&imgs[i], &geo[i], true);
+        if (st != JDEC_OK) return st;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return JDEC_ECUDA;
+    if (dev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return JDEC_ECUDA;
+    const jdec_status st = jdec::decode_host_many(ctx, imgs, geo.data(), n, static_cast<cudaStream_t>(stream));
+    if (dev != ctx->device) cudaSetDevice(dev);
+    return st;
+}

@@ -51,10 +51,12 @@ struct jdec_ctx {
     jdec::TuneEntry tune[64];
     int n_tune = 0;
     // host-buffer path: device staging
-    void *h_coef = nullptr;
-    size_t h_coef_cap = 0;
-    void *h_rgb = nullptr;
-    size_t h_rgb_cap = 0;
+    // device staging of the host-buffer calls: two slots, so that consecutive
+    // images of one call overlap their copies
+    void *h_coef[2] = {nullptr, nullptr};
+    size_t h_coef_cap[2] = {0, 0};
+    void *h_rgb[2] = {nullptr, nullptr};
+    size_t h_rgb_cap[2] = {0, 0};
     cudaEvent_t band_ev[64];
     int n_band_ev = 0;
     // batched path
@@ -103,6 +105,9 @@ void save_tune_table(jdec_ctx *ctx);
 void autotune_shape(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cudaStream_t s);
 
 jdec_status decode_host_banded(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cudaStream_t s);
+// n images from host buffers in one call: copies and decodes of consecutive
+// images overlap (alternating staging slots); stream-ordered on s as a whole.
+jdec_status decode_host_many(jdec_ctx *ctx, const jdec_image *imgs, const Geometry *geo, int n, cudaStream_t s);
 jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStream_t s);
 void release_runtime(jdec_ctx *ctx);
 jdec_status decode_jpeg(jdec_ctx *ctx, const uint8_t *data, size_t size, uint8_t *rgb, int64_t pitch, uint32_t flags,

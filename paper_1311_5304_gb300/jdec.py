@@ -88,6 +88,8 @@ def load(build_if_missing: bool = True, path: str | None = None):
         lib.jdec_decode_batch.restype = ctypes.c_int
         lib.jdec_decode_host.argtypes = [P, ctypes.POINTER(Image), P]
         lib.jdec_decode_host.restype = ctypes.c_int
+        lib.jdec_decode_host_batch.argtypes = [P, ctypes.POINTER(Image), ctypes.c_int32, P]
+        lib.jdec_decode_host_batch.restype = ctypes.c_int
         lib.jdec_sync_status.argtypes = [P, P]
         lib.jdec_sync_status.restype = ctypes.c_int
         lib.jdec_destroy.argtypes = [P]
@@ -116,7 +118,7 @@ def status_str(status: int) -> str:
 def exported_symbols() -> list[str]:
     return ["jdec_create", "jdec_decode_coeffs", "jdec_decode_batch", "jdec_decode_host",
             "jdec_sync_status", "jdec_destroy", "jdec_status_str", "jdec_jpeg_parse", "jdec_entropy_decode",
-            "jdec_decode_batch_static", "jdec_decode_jpeg", "jdec_entropy_decode_mt"]
+            "jdec_decode_batch_static", "jdec_decode_jpeg", "jdec_entropy_decode_mt", "jdec_decode_host_batch"]
 
 
 def decode_batch_static(imgs, stream=None, check=True) -> int:
@@ -296,6 +298,15 @@ class Context:
         st = self._lib.jdec_decode_host(self._h, ctypes.byref(img), ctypes.c_void_p(_stream_ptr(stream)))
         if check and st != OK:
             raise JdecError(st, "jdec_decode_host")
+        return st
+
+    def decode_host_batch(self, imgs, stream=None, check=True) -> int:
+        """Host-buffer images in one call; consecutive images' copies and
+        decoding overlap (jdec_decode_host_batch)."""
+        arr = (Image * len(imgs))(*imgs)
+        st = self._lib.jdec_decode_host_batch(self._h, arr, len(imgs), ctypes.c_void_p(_stream_ptr(stream)))
+        if check and st != OK:
+            raise JdecError(st, "jdec_decode_host_batch")
         return st
 
     def sync(self, stream=None, check=True) -> int:
