@@ -140,8 +140,9 @@ JDEC_API jdec_status jdec_decode_host(jdec_ctx *ctx, const jdec_image *img, void
 
 /* jdec_decode_host for n images in one call: the images are decoded in order,
  * and the copies and decoding of consecutive images overlap (the library
- * stages them in two alternating sets of device buffers it owns, sized for
- * the largest two images).  Stream-ordered on `stream` as a whole: the call
+ * stages them in two alternating sets of device buffers it owns; each set
+ * grows to the largest image staged in it and counts against the HBM
+ * budget).  Stream-ordered on `stream` as a whole: the call
  * starts after earlier work on the stream, and later work waits for the last
  * copy back.  Every description is validated before anything is enqueued
  * (first invalid one -> its status, nothing launched).  Results are identical
