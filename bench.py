@@ -497,8 +497,18 @@ def bench_jpeg(ctx, dev, stream, reps=3):
         return min(ts) * 1e3
 
     t_serial = timed(serial)
+    t_huff = timed(lambda: jdec.entropy_decode(data, hplanes))
     t_pipe1 = timed(lambda: ctx.decode_jpeg(data, rgb, threads=1, stream=stream))
     t_pipen = timed(lambda: ctx.decode_jpeg(data, rgb, threads=ncores, stream=stream))
+    # chunk-size profile of the 1-thread pipeline (Sec. 4.5 picks the largest
+    # chunk among the fastest)
+    my = info.blocks_h[0] // 2
+    prof = {}
+    for rows in (my, my // 4, my // 16, my // 64, 1):
+        with jdec.Context(device=dev.index, jpeg_chunk_rows=rows) as c2:
+            prof[rows] = timed(lambda: c2.decode_jpeg(data, rgb, threads=1, stream=stream))
+    best = min(prof.values())
+    pick = max(r for r, t in prof.items() if t <= 1.02 * best)
     mpix = SIDE * SIDE / 1e6
     return {"workload": "8192x8192 4:2:0 q90 texture JPEG, restart interval = 1 MCU row",
             "jpeg_mbytes": round(len(data) / 1e6, 1), "host_cores": ncores,
@@ -507,7 +517,11 @@ def bench_jpeg(ctx, dev, stream, reps=3):
             "pipelined_1_thread": {"ms": round(t_pipe1, 1), "mpix_s": round(mpix / t_pipe1 * 1e3, 1),
                                    "api": "jdec_decode_jpeg threads=1"},
             "pipelined_all_cores": {"ms": round(t_pipen, 1), "mpix_s": round(mpix / t_pipen * 1e3, 1),
-                                    "api": f"jdec_decode_jpeg threads={ncores}"}}
+                                    "api": f"jdec_decode_jpeg threads={ncores}"},
+            "huffman_1_thread_ms": round(t_huff, 1),
+            "amdahl_max_speedup_1_thread": round(t_serial / t_huff, 4),
+            "chunk_profile_1_thread": {"ms_by_chunk_mcu_rows": {str(r): round(t, 1) for r, t in prof.items()},
+                                       "picked_mcu_rows": pick}}
 
 
 def bench_serving(ctx, dev, rates, max_requests, budget_gb):

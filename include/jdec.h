@@ -94,6 +94,10 @@ typedef struct {
     int max_batch;            /* 0 = default (4096); images per batch call   */
     int autotune;             /* 1 = time tile shapes on first use per shape */
     const char *tune_file;    /* NULL or a JSON file to load/save tile picks */
+    int jpeg_chunk_rows;      /* MCU rows per chunk of jdec_decode_jpeg's
+                                 pipeline (rounded up to whole restart
+                                 intervals when decoding in parallel);
+                                 <= 0 = automatic                            */
 } jdec_options;               /* a NULL options pointer = all defaults       */
 
 typedef struct {

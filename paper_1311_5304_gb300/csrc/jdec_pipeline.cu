@@ -115,15 +115,16 @@ jdec_status decode_jpeg(jdec_ctx *ctx, const uint8_t *data, size_t size, uint8_t
     for (int c = 0; c < ncomp; ++c)
         hplanes[c] = reinterpret_cast<int16_t *>(static_cast<uint8_t *>(ctx->p_host) + off[c]);
 
-    // chunk boundaries (about 8 chunks per worker when decoding in parallel)
+    // chunk boundaries: the context's chunk size, else 8 chunks (about 8
+    // per worker when decoding in parallel); parallel chunks are whole
+    // restart intervals
     const int my = g.mcus_y;
     const int step = scan_row_step(J);
     const bool parallel = threads > 1 && step > 0 && step < my && scan_prepare_independent(J) == JDEC_OK;
     int chunk = std::max(1, (my + 7) / 8);
-    if (parallel) {
-        const int want = std::max(1, my / (8 * threads));
-        chunk = std::max(step, (want + step - 1) / step * step);
-    }
+    if (ctx->opt.jpeg_chunk_rows > 0) chunk = std::min(ctx->opt.jpeg_chunk_rows, my);
+    else if (parallel) chunk = std::max(1, my / (8 * threads));
+    if (parallel) chunk = std::max(step, (chunk + step - 1) / step * step);
     std::vector<int> b;
     for (int r = 0; r < my; r += chunk) b.push_back(r);
     while (b.size() > 64) {   // bounded number of events per call

@@ -42,7 +42,7 @@ class JpegInfo(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("tune_file", ctypes.c_char_p)]
+                ("autotune", ctypes.c_int), ("tune_file", ctypes.c_char_p), ("jpeg_chunk_rows", ctypes.c_int)]
 
 
 class Image(ctypes.Structure):
@@ -238,10 +238,10 @@ class Context:
     """One ``jdec_ctx`` (not thread-safe: one per host thread)."""
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_batch: int = 0,
-                 autotune: bool = False, tune_file: str | None = None):
+                 autotune: bool = False, tune_file: str | None = None, jpeg_chunk_rows: int = 0):
         self._lib = load()
         self._opt = Options(int(device), int(hbm_budget_bytes), int(max_batch), int(bool(autotune)),
-                            tune_file.encode() if tune_file else None)
+                            tune_file.encode() if tune_file else None, int(jpeg_chunk_rows))
         h = ctypes.c_void_p()
         st = self._lib.jdec_create(ctypes.byref(h), ctypes.byref(self._opt))
         if st != OK:

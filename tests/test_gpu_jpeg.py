@@ -88,3 +88,22 @@ def test_grayscale_stream(ctx, orc, restart):
         assert_same(host[:, :3 * img.width].reshape(img.height, img.width, 3), want,
                     f"gray restart={restart} threads={threads}")
         assert np.all(host[:, 3 * img.width:] == POISON)
+
+
+@pytest.mark.parametrize("chunk_rows", [1, 2, 7, 1000])
+@pytest.mark.parametrize("sampling", ["420", "422"])
+def test_chunk_size_option(orc, sampling, chunk_rows):
+    # the context's chunk size (Sec. 4.5's profiled parameter) changes only
+    # the pipelining, never the bytes: 1-thread chunks of any height, and
+    # restart-aligned parallel chunks (rounded up to whole intervals of 3 rows)
+    img = synth.make_image(613, 407, sampling, 85, seed=41, kind="texture", sigma=4, fancy=True)
+    mx = img.planes[0].shape[1] // img.h_samp[0]
+    data = synth.encode_jfif(img, 3 * mx)
+    want = oracle_rgb(orc, img)
+    with jdec.Context(jpeg_chunk_rows=chunk_rows) as c:
+        for threads in (1, 6):
+            buf = _rgb(img.height, img.width)
+            c.decode_jpeg(data, buf, threads=threads)
+            c.sync()
+            got = buf.cpu().numpy().reshape(img.height, img.width, 3)
+            assert_same(got, want, f"{sampling} chunk_rows={chunk_rows} threads={threads}")
