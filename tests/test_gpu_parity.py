@@ -50,6 +50,17 @@ def test_multi_strip_multi_chunk(ctx, orc, sampling, fancy):
         assert_same(got, oracle_rgb(orc, img), f"{sampling} fancy={fancy} {w}x{h}")
 
 
+@pytest.mark.parametrize("sampling,fancy", [("420", True), ("444", True), ("422", False), ("440", True)])
+def test_maximum_width_and_height(ctx, orc, sampling, fancy):
+    # the largest dimension the boundary accepts (65535), thin and wide: a
+    # ragged last MCU column / row, thousands of strips, one strip of many rows
+    rng = np.random.default_rng(zlib.crc32(f"max{sampling}{fancy}".encode()))
+    for (w, h) in [(65535, 37), (23, 65535), (65535, 1031)]:
+        img = synth.random_image(rng, w, h, sampling, fancy=fancy)
+        got, _, _ = gpu_rgb(ctx, img)
+        assert_same(got, oracle_rgb(orc, img), f"{sampling} fancy={fancy} {w}x{h}")
+
+
 @pytest.mark.parametrize("sampling,fancy", MODES)
 def test_synthetic_content(ctx, orc, sampling, fancy):
     img = synth.make_image(1920, 1080, sampling, 85, seed=99, kind="texture", sigma=4.0, fancy=fancy)
