@@ -366,21 +366,38 @@ __device__ __forceinline__ void idct_block_aan(uint32_t blk, const int *__restri
 }
 
 // ---------------------------------------------------------------------------
-// Colour conversion (Sec. 4.3, Alg. 2) in 16-bit fixed point with the
-// chroma offset and the rounding folded into one constant per channel:
-//   R = Y + ((91881 Cr - 11728000) >> 16)
-//   G = Y + ((-22554 Cb - 46802 Cr + 8910336) >> 16)
-//   B = Y + ((116130 Cb - 14831872) >> 16)
-// (91881 = round(1.402 * 2^16), 22554, 46802, 116130 likewise; the constant
-// terms are -c*128*2^16/2^16 + 2^15.)  Y enters as Y * 2^16 before the shift,
-// which is exact.  Saturation happens in the byte pack.
+// Colour conversion (Sec. 4.3, Alg. 2) in 16-bit fixed point.  The chroma
+// samples reach it already offset (C' = C - 128: the upsampling filters fold
+// the -128 into their rounding constants, and unfiltered samples are read as
+// signed bytes of the word XOR 0x80808080), and the luma sample arrives as
+// Y * 2^16 + 2^15 (one byte permute places Y and the rounding constant), so
+// each channel is one multiply-add and one shift:
+//   R = (Y 2^16 + 2^15 + 91881 Cr') >> 16
+//   G = (Y 2^16 + 2^15 - 22554 Cb' - 46802 Cr') >> 16
+//   B = (Y 2^16 + 2^15 + 116130 Cb') >> 16
+// (91881 = round(1.402 * 2^16), 22554, 46802, 116130 likewise); the same
+// integers as Y + ((c Cr' + 2^15) >> 16), because Y * 2^16 is a multiple of
+// 2^16.  Saturation happens in the byte pack.
 // ---------------------------------------------------------------------------
 
-// Byte k of w as an int / placed at bits 16..23 (PRMT with zero fill).
+// Byte k of w as an int (PRMT with zero fill).
 __device__ __forceinline__ int byte_of(uint32_t w, int k) { return static_cast<int>(__byte_perm(w, 0u, 0x4440u | k)); }
-__device__ __forceinline__ int byte_hi16(uint32_t w, int k)
+
+// Byte k of w as a sign-extended int (PRMT sign mode: the msb of a selector
+// nibble replicates the sign of the selected byte).  On a word XORed with
+// 0x80808080 this is the sample minus 128.
+__device__ __forceinline__ int sbyte_of(uint32_t w, int k)
 {
-    return static_cast<int>(__byte_perm(w, 0u, 0x4044u | (static_cast<uint32_t>(k) << 8)));
+    const uint32_t s = static_cast<uint32_t>(k) | ((8u | k) << 4) | ((8u | k) << 8) | ((8u | k) << 12);
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(w), "r"(0u), "r"(s));
+    return static_cast<int>(r);
+}
+
+// Byte k of w placed at bits 16..23 with 0x80 at bits 8..15: Y * 2^16 + 2^15.
+__device__ __forceinline__ int y_term(uint32_t w, int k)
+{
+    return static_cast<int>(__byte_perm(w, 0x8000u, 0x4054u | (static_cast<uint32_t>(k) << 8)));
 }
 
 // Bytes [i, i+4) and [i, i+2) of the 24 little-endian bytes in w (i a
@@ -450,16 +467,17 @@ __device__ __forceinline__ void store24(uint8_t *out, const uint32_t w[6])
 }
 
 // Converts 8 pixels and writes 24 bytes to `out` (global).  yw: the 8 luma
-// samples as two words; `n` = pixels inside the image (1..8).
+// samples as two words; Cb, Cr: chroma minus 128; `n` = pixels inside the
+// image (1..8).
 __device__ __forceinline__ void cc_store8(uint2 yw, const int Cb[8], const int Cr[8], uint8_t *out, int n, bool vec)
 {
     int R[8], G[8], B[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const int ys = byte_hi16(k < 4 ? yw.x : yw.y, k & 3);
-        R[k] = (ys + Cr[k] * 91881 - 11728000) >> 16;
-        G[k] = (ys - Cb[k] * 22554 - Cr[k] * 46802 + 8910336) >> 16;
-        B[k] = (ys + Cb[k] * 116130 - 14831872) >> 16;
+        const int ys = y_term(k < 4 ? yw.x : yw.y, k & 3);
+        R[k] = (ys + Cr[k] * 91881) >> 16;
+        G[k] = (ys - Cb[k] * 22554 - Cr[k] * 46802) >> 16;
+        B[k] = (ys + Cb[k] * 116130) >> 16;
     }
     if (n == 8) {
         uint32_t w[6];
@@ -517,19 +535,21 @@ __device__ __forceinline__ void load10(const uint8_t *p, int c[10])
     c[9] = byte_of(r, 0);
 }
 
-// Alg. 1 (h2v1 triangular) for four centres c[1..4] with neighbours c[0], c[5].
+// Alg. 1 (h2v1 triangular) for four centres c[1..4] with neighbours c[0],
+// c[5]; outputs minus 128 ((x - 512) >> 2 = (x >> 2) - 128).
 __device__ __forceinline__ void tri_h2v1(const int c[6], int o[8])
 {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int t = 3 * c[k + 1];
-        o[2 * k] = (t + c[k] + 1) >> 2;
-        o[2 * k + 1] = (t + c[k + 2] + 2) >> 2;
+        o[2 * k] = (t + c[k] + 1 - 512) >> 2;
+        o[2 * k + 1] = (t + c[k + 2] + 2 - 512) >> 2;
     }
 }
 
 // h2v2 triangular: vertical 3:1 sums of the near and far rows, then the
-// horizontal 3:1 filter with one rounding (+8 / +7, >> 4).
+// horizontal 3:1 filter with one rounding (+8 / +7, >> 4); outputs minus 128
+// ((x - 2048) >> 4 = (x >> 4) - 128).
 __device__ __forceinline__ void tri_h2v2(const int n[6], const int f[6], int o[8])
 {
     int s[6];
@@ -538,8 +558,8 @@ __device__ __forceinline__ void tri_h2v2(const int n[6], const int f[6], int o[8
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int t = 3 * s[k + 1];
-        o[2 * k] = (t + s[k] + 8) >> 4;
-        o[2 * k + 1] = (t + s[k + 2] + 7) >> 4;
+        o[2 * k] = (t + s[k] + 8 - 2048) >> 4;
+        o[2 * k + 1] = (t + s[k + 2] + 7 - 2048) >> 4;
     }
 }
 

@@ -116,27 +116,32 @@ __device__ __forceinline__ void cc_task(const ItemDesc &d, const SmemLayout &L, 
     int Cb[2][8], Cr[2][8];
     if (HM == 1) {
         // 4:4:4: chroma sample = pixel; 4:4:0 replication: chroma row y/2
+        // (samples minus 128: signed bytes of the words XOR 0x80808080)
         const uint8_t *cb = slot + (VM == 2 ? (py >> 1) : py) * L.lc + 16 * gt;
-        const uint4 wb = *reinterpret_cast<const uint4 *>(cb);
-        const uint4 wr = *reinterpret_cast<const uint4 *>(cb + 8 * L.lc);
+        uint4 wb = *reinterpret_cast<const uint4 *>(cb);
+        uint4 wr = *reinterpret_cast<const uint4 *>(cb + 8 * L.lc);
+        wb.x ^= 0x80808080u; wb.y ^= 0x80808080u; wb.z ^= 0x80808080u; wb.w ^= 0x80808080u;
+        wr.x ^= 0x80808080u; wr.y ^= 0x80808080u; wr.z ^= 0x80808080u; wr.w ^= 0x80808080u;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            Cb[0][k] = byte_of(wb.x, k); Cb[0][4 + k] = byte_of(wb.y, k);
-            Cb[1][k] = byte_of(wb.z, k); Cb[1][4 + k] = byte_of(wb.w, k);
-            Cr[0][k] = byte_of(wr.x, k); Cr[0][4 + k] = byte_of(wr.y, k);
-            Cr[1][k] = byte_of(wr.z, k); Cr[1][4 + k] = byte_of(wr.w, k);
+            Cb[0][k] = sbyte_of(wb.x, k); Cb[0][4 + k] = sbyte_of(wb.y, k);
+            Cb[1][k] = sbyte_of(wb.z, k); Cb[1][4 + k] = sbyte_of(wb.w, k);
+            Cr[0][k] = sbyte_of(wr.x, k); Cr[0][4 + k] = sbyte_of(wr.y, k);
+            Cr[1][k] = sbyte_of(wr.z, k); Cr[1][4 + k] = sbyte_of(wr.w, k);
         }
     } else if (!FANCY) {
-        // replication: chroma sample (x/2, y/VM)
+        // replication: chroma sample (x/2, y/VM), minus 128 as above
         const uint8_t *cb = slot + (VM == 2 ? (py >> 1) : py) * L.lc + 8 * gt;
-        const uint2 wb = *reinterpret_cast<const uint2 *>(cb);
-        const uint2 wr = *reinterpret_cast<const uint2 *>(cb + 8 * L.lc);
+        uint2 wb = *reinterpret_cast<const uint2 *>(cb);
+        uint2 wr = *reinterpret_cast<const uint2 *>(cb + 8 * L.lc);
+        wb.x ^= 0x80808080u; wb.y ^= 0x80808080u;
+        wr.x ^= 0x80808080u; wr.y ^= 0x80808080u;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            Cb[0][2 * k] = Cb[0][2 * k + 1] = byte_of(wb.x, k);
-            Cb[1][2 * k] = Cb[1][2 * k + 1] = byte_of(wb.y, k);
-            Cr[0][2 * k] = Cr[0][2 * k + 1] = byte_of(wr.x, k);
-            Cr[1][2 * k] = Cr[1][2 * k + 1] = byte_of(wr.y, k);
+            Cb[0][2 * k] = Cb[0][2 * k + 1] = sbyte_of(wb.x, k);
+            Cb[1][2 * k] = Cb[1][2 * k + 1] = sbyte_of(wb.y, k);
+            Cr[0][2 * k] = Cr[0][2 * k + 1] = sbyte_of(wr.x, k);
+            Cr[1][2 * k] = Cr[1][2 * k + 1] = sbyte_of(wr.y, k);
         }
     } else {
         // h2v1 triangular (Alg. 1); the slot row starts one halo block left
@@ -232,8 +237,9 @@ __device__ __forceinline__ void cc_task_h1v2_pair(const ItemDesc &d, const SmemL
         for (int k = 0; k < 8; ++k) {
             const uint32_t sel = k < 4 ? 0 : 1;
             const int near = 3 * byte_of(sel ? wn.y : wn.x, k & 3);
-            c0[k] = (near + byte_of(sel ? wu.y : wu.x, k & 3) + 1) >> 2;
-            c1[k] = (near + byte_of(sel ? wd.y : wd.x, k & 3) + 2) >> 2;
+            // minus 128: (x - 512) >> 2 = (x >> 2) - 128
+            c0[k] = (near + byte_of(sel ? wu.y : wu.x, k & 3) + 1 - 512) >> 2;
+            c1[k] = (near + byte_of(sel ? wd.y : wd.x, k & 3) + 2 - 512) >> 2;
         }
     }
     uint8_t *out = d.rgb + static_cast<int64_t>(y) * d.pitch + 3 * x0;
