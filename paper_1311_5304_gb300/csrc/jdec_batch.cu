@@ -1,8 +1,8 @@
 // jdec_batch.cu -- batched decoding of many images in one CUDA graph.
 //
 // Host side of jdec_decode_batch: every image is cut into strips of its
-// variant's width; for each variant class (sampling, upsampling, 8-bit or
-// 16-bit tables) the strips' MCU rows of its images, concatenated image after
+// variant's width; for each variant class (sampling, upsampling, and the
+// dequantisation/IDCT mode: LLM with 8-bit or 16-bit tables, or AAN) the strips' MCU rows of its images, concatenated image after
 // image, are weighted by their decode cost and split into equal contiguous
 // shares, one per resident CTA of that class's kernel.  Each class runs as one
 // persistent launch over its (image, strip, row range) work list, holding
