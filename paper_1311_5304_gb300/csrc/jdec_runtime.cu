@@ -70,9 +70,9 @@ void load_tune_table(jdec_ctx *ctx)
     fclose(f);
     buf[n] = 0;
     const char *p = strstr(buf.data(), "\"sms\"");
-    if (!p) return;
+    if (!p || !(p = strchr(p, ':'))) return;   // malformed: ignore
     int sms = 0;
-    if (sscanf(strchr(p, ':') + 1, "%d", &sms) != 1 || sms != ctx->sms) return;   // other GPU: ignore
+    if (sscanf(p + 1, "%d", &sms) != 1 || sms != ctx->sms) return;   // other GPU: ignore
     p = strstr(buf.data(), "\"entries\"");
     if (!p) return;
     p = strchr(p, '[');

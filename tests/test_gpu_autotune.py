@@ -43,3 +43,13 @@ def test_table_of_another_gpu_is_ignored(orc, tmp_path):
     with jdec.Context(tune_file=str(path)) as ctx:
         got, _, _ = gpu_rgb(ctx, img)
     assert_same(got, oracle_rgb(orc, img), "foreign table")
+
+
+@pytest.mark.parametrize("text", ['{"sms"', '{"sms": }', '{"gpu": "x", "sms": 152, "entries": [[4, 5', "", "\x00\xff"])
+def test_malformed_table_is_ignored(orc, tmp_path, text):
+    path = tmp_path / "tune.json"
+    path.write_bytes(text.encode("latin-1"))
+    img = synth.make_image(640, 480, "420", 80, seed=3, kind="texture", sigma=4, fancy=True)
+    with jdec.Context(tune_file=str(path)) as ctx:
+        got, _, _ = gpu_rgb(ctx, img)
+    assert_same(got, oracle_rgb(orc, img), "malformed table")
