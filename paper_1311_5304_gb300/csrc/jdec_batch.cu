@@ -146,8 +146,10 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
         ctx->batch = new (std::nothrow) BatchState();
         if (!ctx->batch) return JDEC_ENOMEM;
         if (cudaEventCreateWithFlags(&ctx->batch->copied, cudaEventDisableTiming) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&ctx->batch->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+            cudaStreamCreateWithFlags(&ctx->batch->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            release_batch(ctx);   // a later call starts over instead of using half-made state
             return JDEC_ECUDA;
+        }
     }
     BatchState *b = ctx->batch;
 

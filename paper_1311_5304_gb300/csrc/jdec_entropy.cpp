@@ -312,6 +312,8 @@ jdec_status decode_mcus(const Parsed &P, ScanState &S, int16_t *const planes[3],
                 // the reader may have buffered padding bits only; skip to the marker
                 while (q + 1 < br.end && !(q[0] == 0xFF && q[1] != 0x00)) ++q;
             }
+            // fill bytes (0xFF) may precede any marker (T.81 B.1.1.2)
+            while (q + 2 < br.end && q[0] == 0xFF && q[1] == 0xFF) ++q;
             if (!(q + 1 < br.end && q[0] == 0xFF && q[1] >= 0xD0 && q[1] <= 0xD7)) return JDEC_EINVAL;
             br.reset_at(q + 2);
             S.pred[0] = S.pred[1] = S.pred[2] = 0;

@@ -112,3 +112,24 @@ def test_grayscale_streams(restart):
         plane = np.zeros((info.blocks_h[0], info.blocks_w[0], 64), np.int16)
         jdec.entropy_decode(data, [plane], threads=threads)
         assert np.array_equal(plane, img.planes[0])
+
+
+def test_fill_bytes_before_restart_markers():
+    # T.81 B.1.1.2: any marker may be preceded by fill bytes 0xFF; the one-
+    # thread and the restart-parallel decoders both accept them
+    img = synth.make_image(64, 48, "420", 80, seed=6, kind="texture", sigma=4)
+    mx = img.planes[0].shape[1] // 2
+    data = synth.encode_jfif(img, mx)
+    filled = bytearray()
+    i = 0
+    while i < len(data):
+        if data[i] == 0xFF and i + 1 < len(data) and 0xD0 <= data[i + 1] <= 0xD7:
+            filled += b"\xff\xff\xff"
+        filled.append(data[i])
+        i += 1
+    info = jdec.jpeg_parse(bytes(filled))
+    for threads in (1, 4):
+        planes = [np.zeros((info.blocks_h[c], info.blocks_w[c], 64), np.int16) for c in range(3)]
+        jdec.entropy_decode(bytes(filled), planes, threads=threads)
+        for c in range(3):
+            assert np.array_equal(planes[c], img.planes[c])
