@@ -44,6 +44,8 @@ def test_null_arguments_are_rejected_without_a_device():
     assert lib.jdec_decode_coeffs(None, None, None) == jdec.EINVAL
     assert lib.jdec_decode_batch(None, None, 0, None) == jdec.EINVAL
     assert lib.jdec_decode_host(None, None, None) == jdec.EINVAL
+    assert lib.jdec_decode_host_batch(None, None, 1, None) == jdec.EINVAL
+    assert lib.jdec_decode_jpeg(None, None, 0, None, 0, 0, 1, None) == jdec.EINVAL
     assert lib.jdec_sync_status(None, None) == jdec.EINVAL
     assert lib.jdec_destroy(None) == jdec.EINVAL
 
