@@ -116,8 +116,9 @@ def kernel_source_sha() -> str:
 
 
 def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+    """DRAM bytes (read + write) of one step's three launches from the
+    committed ncu summary, if it was taken on the current kernel sources
+    (else None)."""
     path = os.path.join(ROOT, "profiles", "fused_kernel_8192_ncu.md")
     try:
         txt = open(path).read()

@@ -1,0 +1,37 @@
+"""Host-side pieces of bench.py that decide what it reports: the source hash
+that ties the committed ncu traffic figure to the kernel sources it was
+measured on, and the whole-job throughput arithmetic."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_code_hash_ignores_comments_and_layout():
+    a = "int x = 1; // note\n/* block\n comment */ int y;"
+    b = "int x = 1;\n\n   int y;   // other note"
+    assert bench._code_only(a) == bench._code_only(b) == "int x = 1; int y;"
+    assert bench._code_only("int x = 2;") != bench._code_only("int x = 1;")
+
+
+def test_committed_traffic_is_plausible_for_the_step():
+    traffic = bench.profiled_traffic()
+    if traffic is None:
+        pytest.skip("the committed ncu summary was taken on other kernel sources")
+    # algorithmic bytes of the step: 128 B per padded block + 3 B per pixel
+    side = bench.SIDE
+    px = side * side
+    blocks = {"444": 3 * px // 64, "422": 2 * px // 64, "420": 3 * px // 128}
+    alg = sum(128 * b + 3 * px for b in blocks.values())
+    # reads = coefficients + chroma halo, writes <= RGB (part stays in L2)
+    assert 0.7 * alg < traffic < 1.1 * alg
+
+
+def test_whole_job_throughput():
+    # 2 ranks, 3 steps of 1e6 pixels each, slowest rank 1.5 ms: 4000 MPix/s
+    assert bench.whole_job_mpix_s(1e6, 3, 2, 1.5) == pytest.approx(4000.0)
