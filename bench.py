@@ -300,7 +300,7 @@ def run_ours(args, ws, rank, local):
            "warmup": args.warmup, "ms_per_step": round(elapsed_ms / K, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded)",
            "config": {"workload": workload, "images_per_step": len(imgs), "mpix_per_step": px_step / 1e6,
-                      "seed": SEED, "l2": (f"inputs larger than L2 ({tot_bytes / 1e9:.2f} GB moved per step)" if tot_bytes > L2_BYTES
+                      "seed": SEED, "kernel_source_sha": kernel_source_sha(), "l2": (f"inputs larger than L2 ({tot_bytes / 1e9:.2f} GB moved per step)" if tot_bytes > L2_BYTES
                                  else f"inputs fit in L2 ({tot_bytes / 1e9:.3f} GB per step): not a roofline measurement"),
                       "parallelism": f"replicas x{ws}"},
            "e2e": e2e, "roofline": roofline, "clocks": clocks, "gpu_launches": len(descs) * K}
