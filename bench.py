@@ -184,7 +184,7 @@ class ClockSampler:
 
 def run_ours(args, ws, rank, local):
     import torch
-    from paper_1311_5304_gb300 import jdec
+    from paper_1311_5304_gb300 import jdec, synth
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -291,7 +291,8 @@ def run_ours(args, ws, rank, local):
                                                                     (99 * len(launch_ms[i])) // 100)], 4),
                                    "gbs": round(bytes_v[i] / (per_var_ms[i] / 1e3) / 1e9, 1),
                                    "frac": round(bytes_v[i] / (per_var_ms[i] / 1e3) / 1e9 / peak, 4),
-                                   "gpix_s": round(imgs[i].width * imgs[i].height / (per_var_ms[i] / 1e3) / 1e9, 1)}
+                                   "gpix_s": round(imgs[i].width * imgs[i].height / (per_var_ms[i] / 1e3) / 1e9, 1),
+                                   "nonzero_ac": round(synth.nonzero_ac_fraction(imgs[i]), 4)}
                                for i, v in enumerate(args.variants)}}
 
     workload = WORKLOAD if default_workload else \
