@@ -131,6 +131,22 @@ def profiled_traffic():
     return float(m_tr.group(1))
 
 
+def profiled_inst_per_px():
+    """Warp instructions per pixel of each variant (4:4:4, 4:2:2, 4:2:0) from
+    the committed ncu summary, if it was taken on the current kernel sources
+    (else None): the ops-per-pixel figure beside the bytes."""
+    path = os.path.join(ROOT, "profiles", "fused_kernel_8192_ncu.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
+    m_row = re.search(r"\|\s*warp instructions per pixel\s*\|\s*([0-9.]+)\s*\|\s*([0-9.]+)\s*\|\s*([0-9.]+)\s*\|", txt)
+    if not m_sha or not m_row or m_sha.group(1) != kernel_source_sha():
+        return None
+    return dict(zip(("444", "422", "420"), (float(m_row.group(i)) for i in (1, 2, 3))))
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples during the timed region."""
 
@@ -280,6 +296,7 @@ def run_ours(args, ws, rank, local):
     default_workload = args.size == (SIDE, SIDE) and args.variants == VARIANTS
     # the committed counters were taken on the default workload only
     traffic = profiled_traffic() if default_workload else None
+    inst_px = profiled_inst_per_px()
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
@@ -292,7 +309,8 @@ def run_ours(args, ws, rank, local):
                                    "gbs": round(bytes_v[i] / (per_var_ms[i] / 1e3) / 1e9, 1),
                                    "frac": round(bytes_v[i] / (per_var_ms[i] / 1e3) / 1e9 / peak, 4),
                                    "gpix_s": round(imgs[i].width * imgs[i].height / (per_var_ms[i] / 1e3) / 1e9, 1),
-                                   "nonzero_ac": round(synth.nonzero_ac_fraction(imgs[i]), 4)}
+                                   "nonzero_ac": round(synth.nonzero_ac_fraction(imgs[i]), 4),
+                                   "warp_inst_per_px": (inst_px or {}).get(v) if default_workload else None}
                                for i, v in enumerate(args.variants)}}
 
     workload = WORKLOAD if default_workload else \
@@ -301,7 +319,8 @@ def run_ours(args, ws, rank, local):
            "warmup": args.warmup, "ms_per_step": round(elapsed_ms / K, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded)",
            "config": {"workload": workload, "images_per_step": len(imgs), "mpix_per_step": px_step / 1e6,
-                      "seed": SEED, "kernel_source_sha": kernel_source_sha(), "l2": (f"inputs larger than L2 ({tot_bytes / 1e9:.2f} GB moved per step)" if tot_bytes > L2_BYTES
+                      "seed": SEED, "kernel_source_sha": kernel_source_sha(),
+                      "sms": torch.cuda.get_device_properties(dev).multi_processor_count, "l2": (f"inputs larger than L2 ({tot_bytes / 1e9:.2f} GB moved per step)" if tot_bytes > L2_BYTES
                                  else f"inputs fit in L2 ({tot_bytes / 1e9:.3f} GB per step): not a roofline measurement"),
                       "parallelism": f"replicas x{ws}"},
            "e2e": e2e, "roofline": roofline, "clocks": clocks, "gpu_launches": len(descs) * K}

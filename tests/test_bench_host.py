@@ -35,3 +35,11 @@ def test_committed_traffic_is_plausible_for_the_step():
 def test_whole_job_throughput():
     # 2 ranks, 3 steps of 1e6 pixels each, slowest rank 1.5 ms: 4000 MPix/s
     assert bench.whole_job_mpix_s(1e6, 3, 2, 1.5) == pytest.approx(4000.0)
+
+
+def test_committed_instruction_counts_are_read():
+    inst = bench.profiled_inst_per_px()
+    if inst is None:
+        pytest.skip("the committed ncu summary was taken on other kernel sources")
+    assert set(inst) == {"444", "422", "420"}
+    assert all(1.0 < v < 3.0 for v in inst.values())
