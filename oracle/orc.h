@@ -21,7 +21,7 @@
  * one choice those pins cannot single out (any accurate factorisation passes
  * them).  It is pinned instead by an independent decoder: NVIDIA's nvJPEG
  * library gives exactly the oracle's RGB bytes (replicated chroma) on the
- * encoder's streams at several qualities and all three samplings
+ * encoder's streams at several qualities, for 4:4:4, 4:2:2, 4:2:0, 4:4:0 and grayscale
  * (tests/test_gpu_nvjpeg.py, which needs the GPU machine).
  */
 #ifndef ORC_H
