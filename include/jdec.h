@@ -57,7 +57,7 @@ typedef enum {
     JDEC_EINVAL = -1,        /* invalid argument or inconsistent geometry   */
     JDEC_ENOMEM = -2,        /* device or pinned-host allocation failed     */
     JDEC_ECUDA = -3,         /* a CUDA runtime call failed                  */
-    JDEC_EUNSUPPORTED = -4,  /* valid JPEG, but a sampling this build lacks */
+    JDEC_EUNSUPPORTED = -4,  /* valid JPEG, but a sampling or mode the library lacks */
     JDEC_EBUSY = -5,         /* request exceeds the context's HBM budget    */
     JDEC_ETIMEOUT = -6       /* a device-side bounded wait gave up          */
 } jdec_status;

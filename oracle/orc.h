@@ -22,7 +22,7 @@
  * them).  It is pinned instead by an independent decoder: NVIDIA's nvJPEG
  * library gives exactly the oracle's RGB bytes (replicated chroma) on the
  * encoder's streams at several qualities, for 4:4:4, 4:2:2, 4:2:0, 4:4:0 and grayscale
- * (tests/test_gpu_nvjpeg.py, which needs the GPU machine).
+ * (tests/test_gpu_nvjpeg.py, which needs a GPU).
  */
 #ifndef ORC_H
 #define ORC_H
