@@ -340,6 +340,7 @@ def run_ours(args, ws, rank, local):
                                     min(K, args.aan_steps), keep)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(imgs, args.cpu_seconds)
+        out["partition_sps"] = sps_estimate(out, imgs)
     if ws > 1:
         torch.distributed.destroy_process_group()
     ctx.close()
@@ -422,6 +423,32 @@ def bench_aan(ctx, stream, imgs, planes, rgbs, variants, llm_ms, steps, keep):
             "by_variant": {v: {"ms": round(ms[i], 4), "llm_ms": round(llm_ms[i], 4),
                                "gpix_s": round(imgs[i].width * imgs[i].height / (ms[i] / 1e3) / 1e9, 1)}
                            for i, v in enumerate(variants)}}
+
+
+def sps_estimate(out, imgs, dispatch_s=20e-6):
+    """Sec. 5's simple partitioning scheme applied to this step as a planning
+    calculation: the rows the host cores (at the oracle's measured rate)
+    would take so that they finish with the GPU (at the device-resident and
+    at the end-to-end rate), the Newton root of the balance equation.  Not
+    executed: the library has no CPU back-end."""
+    from paper_1311_5304_gb300 import partition
+    w = imgs[0].width
+    h = sum(im.height for im in imgs)           # the step's images stacked
+    cpu_px_s = out["cpu_baseline"]["value"] * 1e6
+    res = {"cpu_px_s": cpu_px_s, "dispatch_s": dispatch_s, "mcu_rows": 16, "executed": False}
+    for name, rate in (("device_resident", out["value"]), ("end_to_end", (out.get("e2e") or {}).get("value"))):
+        if not rate:
+            continue
+        gpu_px_s = rate * 1e6
+        p_cpu = lambda x: x * w / cpu_px_s      # noqa: E731
+        p_gpu = lambda y: y * w / gpu_px_s      # noqa: E731
+        t_disp = lambda y: dispatch_s           # noqa: E731
+        x = partition.sps_split(h, 16, p_cpu, p_gpu, t_disp)
+        t0 = partition.balanced_time(h, 0, p_cpu, p_gpu, t_disp)
+        t1 = partition.balanced_time(h, x, p_cpu, p_gpu, t_disp)
+        res[name] = {"cpu_rows": x, "rows": h, "cpu_share": round(x / h, 5),
+                     "predicted_speedup": round(t0 / t1, 4)}
+    return res
 
 
 def bench_batched(ctx, dev, stream, steps, warmup, nimages=1024):

@@ -43,3 +43,17 @@ def test_committed_instruction_counts_are_read():
         pytest.skip("the committed ncu summary was taken on other kernel sources")
     assert set(inst) == {"444", "422", "420"}
     assert all(1.0 < v < 3.0 for v in inst.values())
+
+
+def test_sps_estimate_from_measured_rates():
+    class Img:
+        width = height = 8192
+    out = {"value": 425000.0, "e2e": {"value": 37000.0}, "cpu_baseline": {"value": 830.0}}
+    est = bench.sps_estimate(out, [Img(), Img(), Img()])
+    assert est["executed"] is False
+    dev, e2e = est["device_resident"], est["end_to_end"]
+    # the host cores are ~500x slower than the device-resident GPU: a sliver
+    assert 0 <= dev["cpu_share"] < 0.005 and dev["predicted_speedup"] >= 1.0
+    # against the link-bound end-to-end rate they could take ~2 %
+    assert 0.01 < e2e["cpu_share"] < 0.04 and e2e["predicted_speedup"] > 1.0
+    assert dev["cpu_rows"] % 16 == 0 and e2e["cpu_rows"] % 16 == 0
