@@ -558,6 +558,16 @@ def bench_jpeg(ctx, dev, stream, reps=3):
     best = min(prof.values())
     pick = max(r for r, t in prof.items() if t <= 1.02 * best)
     mpix = SIDE * SIDE / 1e6
+    # Sec. 5's pipelined partitioning (PPS) for this stream, as a planning
+    # calculation from the measured stages: host Huffman per pixel row (one
+    # thread), the device back-end, and the oracle's one-core rate for the
+    # host's share of the back-end
+    from paper_1311_5304_gb300 import partition
+    huff_row = t_huff / 1e3 / SIDE
+    gpu_row = (t_serial - t_huff) / 1e3 / SIDE
+    cpu_row = SIDE / 64e6                  # ~64 MPix/s: the oracle on one host core
+    pps_rows = partition.pps_split(SIDE, 16, pick * 16, lambda r: r * huff_row, lambda x: x * cpu_row,
+                                   lambda y: y * gpu_row)
     return {"workload": "8192x8192 4:2:0 q90 texture JPEG, restart interval = 1 MCU row",
             "jpeg_mbytes": round(len(data) / 1e6, 1), "host_cores": ncores,
             "serial": {"ms": round(t_serial, 1), "mpix_s": round(mpix / t_serial * 1e3, 1),
@@ -569,7 +579,12 @@ def bench_jpeg(ctx, dev, stream, reps=3):
             "huffman_1_thread_ms": round(t_huff, 1),
             "amdahl_max_speedup_1_thread": round(t_serial / t_huff, 4),
             "chunk_profile_1_thread": {"ms_by_chunk_mcu_rows": {str(r): round(t, 1) for r, t in prof.items()},
-                                       "picked_mcu_rows": pick}}
+                                       "picked_mcu_rows": pick},
+            "partition_pps": {"cpu_rows": pps_rows, "rows": SIDE, "chunk_rows": pick * 16, "executed": False,
+                              "note": ("host rows after the first chunk outlast the device's whole share"
+                                       if huff_row * (SIDE - pick * 16) >= gpu_row * SIDE else
+                                       "one MCU row of host back-end work outlasts the whole device share"
+                                       if pps_rows == 0 else "the host takes rows")}}
 
 
 def bench_serving(ctx, dev, rates, max_requests, budget_gb):

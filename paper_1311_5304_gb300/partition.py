@@ -69,3 +69,14 @@ def balanced_time(h: int, x: int, p_cpu: Cost, p_gpu: Cost, t_dispatch: Cost | N
     T_total = max(T_CPU, T_GPU) without the shared Huffman term)."""
     td = t_dispatch or (lambda y: 0.0)
     return max(td(h - x) + p_cpu(x), p_gpu(h - x))
+
+
+def pps_split(h: int, mcu_rows: int, chunk_rows: int, t_huffman: Cost, p_cpu: Cost, p_gpu: Cost,
+              t_dispatch: Cost | None = None) -> int:
+    """The pipelined scheme of Sec. 5 (PPS): the CPU entropy-decodes the whole
+    image -- all but the first GPU chunk of it while the GPU already works --
+    and then transforms its own x rows, so its side of the balance is
+    T_Huffman(h - c) + P_CPU(x) (+ dispatch), the GPU's P_GPU(h - x).
+    ``t_huffman(rows)``: host decoding time for that many rows."""
+    rest = t_huffman(max(0, h - chunk_rows))
+    return sps_split(h, mcu_rows, lambda x: rest + p_cpu(x), p_gpu, t_dispatch)

@@ -39,3 +39,16 @@ def test_split_never_loses_to_either_side_alone():
     t = partition.balanced_time(h, x, p_cpu, p_gpu)
     assert t <= partition.balanced_time(h, 0, p_cpu, p_gpu) + 1e-12
     assert t <= partition.balanced_time(h, h, p_cpu, p_gpu) + 1e-12
+
+
+def test_pps_counts_the_overlapped_huffman_on_the_cpu_side():
+    h, c = 4096, 256
+    p_cpu = lambda x: 1.0 * x          # noqa: E731
+    p_gpu = lambda y: 1.0 * y          # noqa: E731
+    huff = lambda rows: 0.25 * rows    # noqa: E731
+    x = partition.pps_split(h, 1, c, huff, p_cpu, p_gpu)
+    # 0.25 (h - c) + x = h - x
+    want = (h - 0.25 * (h - c)) / 2
+    assert abs(x - want) <= 1.0
+    # host decoding slower than the GPU's whole share: the CPU takes no rows
+    assert partition.pps_split(h, 16, c, lambda r: 10.0 * r, p_cpu, lambda y: 0.001 * y) == 0
