@@ -198,9 +198,29 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def variant_stats(variants, imgs, bytes_v, per_var_ms, launch_ms, peak, inst_px=None):
+    """Per-variant line of the roofline object: bytes, mean / p50 / p99 launch
+    time, GB/s and fraction of the peak, GPix/s, the workload's nonzero-AC
+    fraction and (when known for these sources) warp instructions per pixel."""
+    from paper_1311_5304_gb300 import synth
+    out = {}
+    for i, v in enumerate(variants):
+        ms = per_var_ms[i]
+        srt = sorted(launch_ms[i])
+        out[v] = {"bytes": bytes_v[i], "ms": round(ms, 4),
+                  "ms_p50": round(srt[len(srt) // 2], 4),
+                  "ms_p99": round(srt[min(len(srt) - 1, (99 * len(srt)) // 100)], 4),
+                  "gbs": round(bytes_v[i] / (ms / 1e3) / 1e9, 1),
+                  "frac": round(bytes_v[i] / (ms / 1e3) / 1e9 / peak, 4),
+                  "gpix_s": round(imgs[i].width * imgs[i].height / (ms / 1e3) / 1e9, 1),
+                  "nonzero_ac": round(synth.nonzero_ac_fraction(imgs[i]), 4),
+                  "warp_inst_per_px": (inst_px or {}).get(v)}
+    return out
+
+
 def run_ours(args, ws, rank, local):
     import torch
-    from paper_1311_5304_gb300 import jdec, synth
+    from paper_1311_5304_gb300 import jdec
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -302,16 +322,8 @@ def run_ours(args, ws, rank, local):
                 "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
                 "kernel": "jdec_fused_kernel (3 variants per step)",
                 "algorithmic_bytes_per_step": tot_bytes,
-                "by_variant": {v: {"bytes": bytes_v[i], "ms": round(per_var_ms[i], 4),
-                                   "ms_p50": round(launch_ms[i][len(launch_ms[i]) // 2], 4),
-                                   "ms_p99": round(launch_ms[i][min(len(launch_ms[i]) - 1,
-                                                                    (99 * len(launch_ms[i])) // 100)], 4),
-                                   "gbs": round(bytes_v[i] / (per_var_ms[i] / 1e3) / 1e9, 1),
-                                   "frac": round(bytes_v[i] / (per_var_ms[i] / 1e3) / 1e9 / peak, 4),
-                                   "gpix_s": round(imgs[i].width * imgs[i].height / (per_var_ms[i] / 1e3) / 1e9, 1),
-                                   "nonzero_ac": round(synth.nonzero_ac_fraction(imgs[i]), 4),
-                                   "warp_inst_per_px": (inst_px or {}).get(v) if default_workload else None}
-                               for i, v in enumerate(args.variants)}}
+                "by_variant": variant_stats(args.variants, imgs, bytes_v, per_var_ms, launch_ms, peak,
+                                            inst_px if default_workload else None)}
 
     workload = WORKLOAD if default_workload else \
         f"{args.size[0]}x{args.size[1]} q90 texture, {'+'.join(args.variants)}, triangular upsampling"

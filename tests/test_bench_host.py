@@ -57,3 +57,19 @@ def test_sps_estimate_from_measured_rates():
     # against the link-bound end-to-end rate they could take ~2 %
     assert 0.01 < e2e["cpu_share"] < 0.04 and e2e["predicted_speedup"] > 1.0
     assert dev["cpu_rows"] % 16 == 0 and e2e["cpu_rows"] % 16 == 0
+
+
+def test_variant_stats_line():
+    from paper_1311_5304_gb300 import synth
+    imgs = [synth.make_image(64, 48, s, 80, seed=1) for s in ("444", "422", "420")]
+    bytes_v = [im.coef_bytes() + im.rgb_bytes() for im in imgs]
+    launch_ms = [[0.2, 0.1, 0.3], [0.1] * 5, [0.05, 0.06]]
+    per_var_ms = [sum(x) / len(x) for x in launch_ms]
+    st = bench.variant_stats(["444", "422", "420"], imgs, bytes_v, per_var_ms, launch_ms, 6674.5,
+                             {"444": 1.9, "422": 1.7, "420": 1.8})
+    assert st["444"]["ms_p50"] == 0.2 and st["444"]["ms_p99"] == 0.3
+    assert st["422"]["warp_inst_per_px"] == 1.7
+    assert 0.0 <= st["420"]["nonzero_ac"] <= 1.0
+    assert st["420"]["gbs"] == round(bytes_v[2] / (per_var_ms[2] / 1e3) / 1e9, 1)
+    assert bench.variant_stats(["444"], imgs[:1], bytes_v[:1], per_var_ms[:1], launch_ms[:1], 1.0)["444"][
+        "warp_inst_per_px"] is None
