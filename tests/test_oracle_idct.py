@@ -201,3 +201,24 @@ def test_aan_and_llm_agree_on_realistic_blocks(orc):
         d = np.abs(a - b)
         assert d.max() <= 1
         assert np.mean(d == 0) > 0.97
+
+
+@pytest.mark.parametrize("aan", [False, True])
+def test_level_shift_inside_the_rounding_constant_is_shift_then_add(orc, aan):
+    # The oracle adds the level shift as 128 * 2^18 (AAN: 128 * 2^15) inside
+    # the row pass's rounding constant.  floor((P + r + 128 * 2^n) / 2^n) is
+    # floor((P + r) / 2^n) + 128 whenever the int32 sum does not wrap, so on
+    # every block of real-data range the samples equal the Eq. 2 output
+    # (idct_core, no level shift) plus 128, then clamped.  They differ only
+    # for adversarial inputs whose sum lies within 2^25 (AAN: 2^22) of the
+    # int32 limit, where both sides of the GPU comparison wrap identically.
+    rng = np.random.default_rng(1805)
+    # dequantised values within the range of 8-bit samples' DCT (|F| < 2^13)
+    q = rng.integers(1, 40, size=64).astype(np.uint16)
+    coef = np.round(rng.laplace(0, 400, size=(4000, 64)) / q).astype(np.int64)
+    coef = np.clip(coef, -(8000 // q.astype(np.int64)), 8000 // q.astype(np.int64)).astype(np.int16)
+    core = orc.idct_core_blocks(coef, q, aan=aan).astype(np.int64)
+    want = np.clip(core + 128, 0, 255)
+    got = orc.idct_blocks(coef, q, aan=aan).astype(np.int64)
+    assert np.array_equal(got, want)
+    assert np.count_nonzero(want == 0) > 0 and np.count_nonzero(want == 255) > 0
