@@ -82,8 +82,9 @@ typedef enum {
  * only): the kernel arms its coefficient-load barriers but issues no loads,
  * so every CTA's bounded wait gives up after its limit (2 s), the CTA stops
  * without writing any pixel, and jdec_sync_status returns JDEC_ETIMEOUT.
- * The context stays usable.  Rejected (JDEC_EINVAL) by the batched and
- * host-buffer calls.  Environment variable JDEC_TEST_FAIL_ALLOCS=n (read by
+ * The context stays usable.  Also accepted by jdec_decode_batch_static
+ * (jdec_batch_static_status then returns JDEC_ETIMEOUT); rejected
+ * (JDEC_EINVAL) by the context-owned batched and host-buffer calls.  Environment variable JDEC_TEST_FAIL_ALLOCS=n (read by
  * jdec_create) makes the context's next n device-buffer allocations fail
  * with JDEC_ENOMEM, for the same purpose. */
 #define JDEC_TEST_WITHHOLD_LOADS 0x80000000u
@@ -119,20 +120,33 @@ typedef struct {
                                      (| JDEC_TEST_*)                            */
 } jdec_image;
 
-/* Creates a context on opt->device (default 0).  *out receives the context. */
+/* Creates a context on opt->device (default 0).  *out receives the context.
+ * No paper passage: context plumbing (device, HBM budget, tile tuner, staging
+ * buffers).  Returns JDEC_EINVAL for a NULL `out` or a bad device ordinal,
+ * JDEC_ENOMEM/JDEC_ECUDA if the runtime cannot set the context up; *out is
+ * then NULL.  The caller owns the context and releases it with jdec_destroy. */
 JDEC_API jdec_status jdec_create(jdec_ctx **out, const jdec_options *opt);
 
-/* Decodes one image with one launch of the fused kernel on `stream`.
- * Coefficient and RGB buffers are owned by the caller and must stay valid
- * until the stream has executed the launch.  Returns JDEC_EINVAL without
- * launching for inconsistent descriptions (see jdec_image). */
+/* Decodes one image with one launch of the fused kernel on `stream`: the
+ * stages of Sec. 4.1 (dequantisation, Eq. 1 column pass, Eq. 2 row pass with
+ * range-limit clamp), Sec. 4.2 (upsampling, Alg. 1), Sec. 4.3 (colour
+ * conversion, Alg. 2) merged into one kernel as Sec. 4.4 merges upsampling
+ * and colour conversion.  Coefficient and RGB buffers are owned by the caller
+ * and must stay valid until the stream has executed the launch.  Returns
+ * JDEC_EINVAL without launching for inconsistent descriptions (see
+ * jdec_image), JDEC_EUNSUPPORTED for other samplings, JDEC_ECUDA if the
+ * launch fails; device-side timeouts are reported by jdec_sync_status. */
 JDEC_API jdec_status jdec_decode_coeffs(jdec_ctx *ctx, const jdec_image *img, void *stream);
 
 /* Decodes n images (any mix of sizes and samplings): per variant class one
- * persistent launch over a flattened MCU work list, the launches recorded
- * once per work-list shape as a CUDA graph and replayed with the descriptors
- * of each call.  Per-image results are identical to jdec_decode_coeffs.
- * n <= max_batch. */
+ * persistent launch over a flattened work list of (image, strip of MCUs, MCU
+ * rows) items -- the paper's grouping of MCUs into work-groups of 4 to 32
+ * MCUs (Sec. 4; sizes profiled per platform, Sec. 5.1) applied across images
+ * -- the launches recorded once per work-list shape as a CUDA graph and
+ * replayed with the descriptors of each call.  Per-image results are
+ * identical to jdec_decode_coeffs.  1 <= n <= max_batch; the first invalid
+ * description's status is returned and nothing is launched.  Buffers as for
+ * jdec_decode_coeffs; descriptors are copied into context-owned buffers. */
 JDEC_API jdec_status jdec_decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int32_t n, void *stream);
 
 /* Same as jdec_decode_coeffs, but coef[] and rgb point to HOST memory
@@ -155,10 +169,12 @@ JDEC_API jdec_status jdec_decode_host_batch(jdec_ctx *ctx, const jdec_image *img
 
 /* Synchronises `stream` and reports any device-side error recorded by earlier
  * launches of this context (a bounded wait that gave up -> JDEC_ETIMEOUT).
- * Clears the recorded error. */
+ * Clears the recorded error.  No paper passage: error plumbing. */
 JDEC_API jdec_status jdec_sync_status(jdec_ctx *ctx, void *stream);
 
-/* Releases the context and every buffer, graph and tensor map it owns. */
+/* Releases the context and every buffer, graph and tensor map it owns
+ * (synchronising its streams first).  No paper passage: context plumbing.
+ * A NULL context returns JDEC_EINVAL. */
 JDEC_API jdec_status jdec_destroy(jdec_ctx *ctx);
 
 /* ---- Host-side entropy decoding (Sec. 2: the sequential stage; Sec. 4.5:
@@ -207,20 +223,34 @@ JDEC_API jdec_status jdec_decode_jpeg(jdec_ctx *ctx, const uint8_t *data, size_t
 
 /* Batched decode for callers that cannot allocate device memory (no
  * counterpart in the paper: a deployment need).  Some callers cannot call
- * cudaMalloc -- code running while a stream is captured into a CUDA graph,
- * processes whose device memory is all reserved by another allocator, paths
- * where the implicit device synchronisation of cudaMalloc/cudaFree is not
- * acceptable.  This call needs no context and allocates nothing: descriptors,
- * work list and error word live in one static device array of 512 KiB that
- * every GPU loading the library holds until exit.  Limits: 1 <= n <= 128
- * images and a work list of at most 16384 items (about 128 images of 4096
- * pixels width); larger requests return JDEC_EINVAL and launch nothing.
- * Results equal jdec_decode_batch.  Runs on the CURRENT device; the first call
- * on a device looks up the array's device address (cudaGetSymbolAddress), so
- * make that first call before any stream capture.  All calls share the array:
- * calls whose work overlaps on the GPU race.  Device-side wait timeouts are
- * recorded in the array, not reported.  Buffers as for jdec_decode_batch. */
+ * cudaMalloc: processes whose device memory is all reserved by another
+ * allocator (a framework's caching pool that holds the whole HBM), and
+ * latency-critical paths where the implicit device-wide synchronisation of
+ * cudaMalloc/cudaFree would stall every other stream.  This call needs no
+ * context and allocates nothing: descriptors, work list and error word live
+ * in one static device array of 512 KiB that every GPU loading the library
+ * holds until exit.  Limits: 1 <= n <= 128 images and a work list of at most
+ * 16384 items (about 64 strips of one MCU row per image at 128 images);
+ * larger requests return JDEC_EINVAL and launch nothing.  Results equal
+ * jdec_decode_batch.  Runs on the CURRENT device; the first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress), so make that
+ * first call before any stream capture.  The descriptors are copied from a
+ * static host buffer with a pageable copy, which waits for earlier work on
+ * `stream` before it starts; the call returns once they are staged.  All calls
+ * share the array and it keeps the last call's contents: calls whose work
+ * overlaps on the GPU (different streams) race.  Device-side wait timeouts are
+ * recorded in the array's error word, which the next call clears; read it
+ * with jdec_batch_static_status before then.  Buffers as for
+ * jdec_decode_batch. */
 JDEC_API jdec_status jdec_decode_batch_static(const jdec_image *imgs, int32_t n, void *stream);
+
+/* Waits for `stream`, then reports the device-side error word that the last
+ * jdec_decode_batch_static call on the current device left in the static
+ * array: JDEC_ETIMEOUT if a bounded device wait gave up (that call's output is
+ * then incomplete), JDEC_OK if none did.  Clears the word.  Allocates nothing
+ * (no counterpart in the paper, like the call it reports on); read it before
+ * the next jdec_decode_batch_static call, which clears the word itself. */
+JDEC_API jdec_status jdec_batch_static_status(void *stream);
 
 /* Static description of a status code. */
 JDEC_API const char *jdec_status_str(jdec_status s);

@@ -13,10 +13,14 @@
 
 namespace jdec {
 
+// The first 1024-byte aligned byte of the dynamic shared-memory window (the
+// 128-byte TMA swizzle repeats every 1024 bytes).  The pointer is formed by
+// adding an offset to the shared array itself, so every pointer derived from
+// it stays a shared-space pointer: shared loads and stores with 32-bit
+// addresses instead of generic ones.
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p)
 {
-    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-    return reinterpret_cast<uint8_t *>((a + 1023) & ~static_cast<uintptr_t>(1023));
+    return p + ((1024u - (smem_u32(p) & 1023u)) & 1023u);
 }
 
 // Raises a kernel's dynamic shared-memory limit to the device's opt-in

@@ -1,16 +1,15 @@
 // jdec_noalloc.cu -- jdec_decode_batch_static: the batched decode for callers
 // that cannot allocate device memory.
 //
-// Some callers of a decoder cannot call cudaMalloc: code that runs while a
-// stream is being captured into a CUDA graph (allocation is not allowed
-// during global-mode capture), processes whose device memory is entirely
-// reserved by another allocator (a framework's caching pool holding the
-// whole HBM), and latency-critical paths where cudaMalloc/cudaFree would
-// synchronise the device.  This entry point therefore owns no context and
-// allocates nothing: the per-image descriptors, the work list and the error
-// word live in one file-scope device array, sized below, that every GPU which
-// loads the library holds until the process exits.  Inputs and outputs are
-// still the caller's buffers.
+// Some callers of a decoder cannot call cudaMalloc: processes whose device
+// memory is entirely reserved by another allocator (a framework's caching
+// pool holding the whole HBM), and latency-critical paths where
+// cudaMalloc/cudaFree would synchronise the whole device and stall every
+// other stream.  This entry point therefore owns no context and allocates
+// nothing: the per-image descriptors, the work list and the error word live
+// in one file-scope device array, sized below, that every GPU which loads the
+// library holds until the process exits.  Inputs and outputs are still the
+// caller's buffers.
 //
 // The array's name is only a host-side stand-in in host code: the first call
 // on each device (with that device current) asks the runtime for its device
@@ -19,7 +18,8 @@
 //
 // Every call shares the array and it keeps the previous call's contents, so
 // calls whose work overlaps on the GPU (on different streams, or a second call
-// before the first has run) race on it.
+// before the first has run) race on it.  Each call clears the error word
+// first; jdec_batch_static_status reads it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -90,7 +90,9 @@ jdec_status decode_batch_static(const jdec_image *imgs, int n, cudaStream_t s)
     if (n < 1 || n > kStaticMaxImages || !imgs) return JDEC_EINVAL;
     std::lock_guard<std::mutex> lock(t_stage_mu);
     for (int i = 0; i < n; ++i) {
-        jdec_status st = validate(&imgs[i], &t_geo[i], false);
+        // the withheld-load testing aid is accepted here: its timeout is read back
+        // through jdec_batch_static_status
+        jdec_status st = validate(&imgs[i], &t_geo[i], false, true);
         if (st != JDEC_OK) return st;
     }
     uint8_t *dscratch = nullptr;
@@ -215,7 +217,29 @@ jdec_status decode_batch_static(const jdec_image *imgs, int n, cudaStream_t s)
     return JDEC_OK;
 }
 
+// Waits for `s`, then reads and clears the static array's error word (a
+// pageable copy into a stack variable: nothing is allocated).
+jdec_status batch_static_status(cudaStream_t s)
+{
+    uint8_t *dscratch = nullptr;
+    int device = 0;
+    jdec_status st = static_scratch(&dscratch, &device);
+    if (st != JDEC_OK) return st;
+    int word = 0;
+    if (cudaMemcpyAsync(&word, dscratch, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return JDEC_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return JDEC_ECUDA;
+    if (word == 0) return JDEC_OK;
+    if (cudaMemsetAsync(dscratch, 0, sizeof(int), s) != cudaSuccess) return JDEC_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return JDEC_ECUDA;
+    return word == kErrTimeout ? JDEC_ETIMEOUT : JDEC_ECUDA;
+}
+
 }  // namespace jdec
+
+extern "C" JDEC_API jdec_status jdec_batch_static_status(void *stream)
+{
+    return jdec::batch_static_status(static_cast<cudaStream_t>(stream));
+}
 
 extern "C" JDEC_API jdec_status jdec_decode_batch_static(const jdec_image *imgs, int32_t n, void *stream)
 {

@@ -98,6 +98,8 @@ def load(build_if_missing: bool = True, path: str | None = None):
         lib.jdec_status_str.restype = ctypes.c_char_p
         lib.jdec_decode_batch_static.argtypes = [ctypes.POINTER(Image), ctypes.c_int32, P]
         lib.jdec_decode_batch_static.restype = ctypes.c_int
+        lib.jdec_batch_static_status.argtypes = [P]
+        lib.jdec_batch_static_status.restype = ctypes.c_int
         lib.jdec_jpeg_parse.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(JpegInfo)]
         lib.jdec_jpeg_parse.restype = ctypes.c_int
         lib.jdec_entropy_decode.argtypes = [P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p * 3)]
@@ -118,7 +120,8 @@ def status_str(status: int) -> str:
 def exported_symbols() -> list[str]:
     return ["jdec_create", "jdec_decode_coeffs", "jdec_decode_batch", "jdec_decode_host",
             "jdec_sync_status", "jdec_destroy", "jdec_status_str", "jdec_jpeg_parse", "jdec_entropy_decode",
-            "jdec_decode_batch_static", "jdec_decode_jpeg", "jdec_entropy_decode_mt", "jdec_decode_host_batch"]
+            "jdec_decode_batch_static", "jdec_decode_jpeg", "jdec_entropy_decode_mt", "jdec_decode_host_batch",
+            "jdec_batch_static_status"]
 
 
 def decode_batch_static(imgs, stream=None, check=True) -> int:
@@ -129,6 +132,12 @@ def decode_batch_static(imgs, stream=None, check=True) -> int:
     if check and st != OK:
         raise JdecError(st, "jdec_decode_batch_static")
     return st
+
+
+def batch_static_status(stream=None) -> int:
+    """Waits for the stream and returns (and clears) the device-side status of
+    the last allocation-free batch call (see jdec_batch_static_status)."""
+    return load().jdec_batch_static_status(ctypes.c_void_p(_stream_ptr(stream)))
 
 
 def jpeg_parse(data) -> JpegInfo:
