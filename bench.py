@@ -505,6 +505,28 @@ def bench_batched(ctx, dev, stream, steps, warmup, nimages=1024):
 
     t_batch = timed(lambda: ctx.decode_batch(descs, stream), steps)
     t_plain = timed(plain, max(1, steps // 2))
+    # autotuned: a context with the batch tuner on; its first call (in the
+    # untimed warm-up) times the candidate shapes per class and keeps the
+    # fastest, later calls replay the tuned graph
+    tune_path = os.path.join(tempfile.mkdtemp(), "batch_tune.json")
+    with jdec.Context(device=dev.index or 0, autotune=True, tune_file=tune_path) as tctx:
+        t0 = time.perf_counter()
+        tctx.decode_batch(descs, stream)
+        tctx.sync(stream)
+        tune_s = time.perf_counter() - t0
+        for _ in range(warmup):
+            tctx.decode_batch(descs, stream)
+        tctx.sync(stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            tctx.decode_batch(descs, stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        tctx.sync(stream)
+        t_tuned = a.elapsed_time(b) / steps
+    with open(tune_path) as f:
+        picks = [e for e in json.load(f)["entries"] if len(e) >= 5 and e[4] == 1]
     peak = float(measured_peaks()[0]["hbm_gbs"])
     return {"workload": f"{nimages} images, W~U[160,4096], H~U[120,3072], 40/30/30% 4:2:0/4:2:2/4:4:4, q~U{{50..95}}",
             "mpix": round(px / 1e6, 1), "gbytes": round(nbytes / 1e9, 2),
@@ -513,9 +535,16 @@ def bench_batched(ctx, dev, stream, steps, warmup, nimages=1024):
                         # one launch per variant class present (all tables here fit 8 bits)
                         "launches": len({sm for (_, _, sm, _) in specs}),
                         "api": "jdec_decode_batch (one persistent launch per variant class, CUDA graph replay)"},
+            "autotuned": {"ms": round(t_tuned, 3), "mpix_s": round(px / t_tuned / 1e3, 1),
+                          "gbs": round(nbytes / t_tuned / 1e6, 1), "frac": round(nbytes / t_tuned / 1e6 / peak, 4),
+                          "tuning_s": round(tune_s, 2),
+                          "picks": [{"class": e[0], "size_class": e[1], "strip_mcus": e[2], "idct_threads": e[3]}
+                                    for e in picks],
+                          "api": "jdec_decode_batch with jdec_options.autotune = 1 (tuned per class and size class)"},
             "plain": {"ms": round(t_plain, 3), "mpix_s": round(px / t_plain / 1e3, 1), "launches": len(descs),
                       "api": "jdec_decode_coeffs per image"},
-            "speedup_batched_vs_plain": round(t_plain / t_batch, 3)}
+            "speedup_batched_vs_plain": round(t_plain / t_batch, 3),
+            "speedup_autotuned_vs_plain": round(t_plain / t_tuned, 3)}
 
 
 def bench_jpeg(ctx, dev, stream, reps=3):
@@ -609,16 +638,21 @@ def bench_serving(ctx, dev, rates, max_requests, budget_gb):
     out = {"mix": "70% 160x160, 25% 1920x1080, 5% 4000x3000; 4:2:0 q~U{80..92}", "hbm_budget_gib": budget_gb}
     for mode in ("full", "coef"):
         pool = serve.request_pool(13115304 + 5000, mode=mode)
-        srv = serve.Server(ctx, device=dev.index or 0, hbm_budget_bytes=int(budget_gb * (1 << 30)))
-        rows = []
-        try:
-            for rate in rates:
-                n = int(min(max_requests, max(200, rate * 0.5)))
-                rows.append(serve.run_load(srv, pool, rate, n, seed=int(rate), mode=mode, timeout=60))
-        finally:
-            srv.close()
-        out[mode] = rows
+        # batched (continuous batching, jdec_decode_batch) and plain (one
+        # jdec_decode_coeffs per request as it is admitted) on the same arrivals
+        for plain in (False, True):
+            srv = serve.Server(ctx, device=dev.index or 0, hbm_budget_bytes=int(budget_gb * (1 << 30)), plain=plain)
+            rows = []
+            try:
+                for rate in rates:
+                    n = int(min(max_requests, max(200, rate * 0.5)))
+                    rows.append(serve.run_load(srv, pool, rate, n, seed=int(rate), mode=mode, timeout=60))
+            finally:
+                srv.close()
+            out[mode + ("_plain" if plain else "")] = rows
         out["host_threads"] = srv.workers
+    out["api"] = {"batched": "serve.Server: jdec_decode_batch over the admitted requests",
+                  "plain": "serve.Server(plain=True): one jdec_decode_coeffs per request"}
     return out
 
 

@@ -9,7 +9,9 @@
 // only that variant's code; the launches follow each other on the stream.
 // The per-image descriptors (TMA tensor maps, geometry, quantisation tables)
 // and the work lists are written to pinned staging memory and copied to a
-// device buffer that the kernels read.  The copy and the launches are
+// device buffer that the kernels read.  Two staging buffers alternate, so a
+// call prepares its work list while the previous call's batch still runs (the
+// host waits only for the batch two calls back).  The copy and the launches are
 // recorded once per launch shape as a CUDA graph and replayed for later calls
 // of the same shape.
 #include <cuda_runtime.h>
@@ -60,6 +62,7 @@ struct ClassLaunch {
 };
 
 struct GraphEntry {
+    int slot;                 // staging buffer the recorded copy reads
     size_t copy_bytes;
     size_t off_items;
     std::vector<ClassLaunch> launches;
@@ -68,18 +71,29 @@ struct GraphEntry {
 
 }  // namespace
 
+// A batch's plan: per image its strip width and class; per class present the
+// union shared-memory layout, the IDCT threads of its split roles and the
+// cost-balanced split of its strip-rows over one wave of that class's CTAs.
+struct Plan {
+    std::vector<int> wt, var, cls_of;
+    int nidct[kClasses];
+    std::vector<ClassLaunch> launches;
+    std::vector<BatchItem> items;
+    std::vector<int32_t> first;
+};
+
 struct BatchState {
     void *d_buf = nullptr;
     size_t d_cap = 0;
-    void *h_buf = nullptr;
-    size_t h_cap = 0;
-    cudaEvent_t copied = nullptr;     // the staging buffer may be rewritten once this fires
-    bool copy_pending = false;
+    void *h_buf[2] = {nullptr, nullptr};
+    size_t h_cap[2] = {0, 0};
+    cudaEvent_t copied[2] = {nullptr, nullptr};   // staging buffer k may be rewritten once copied[k] fires
+    bool copy_pending[2] = {false, false};
+    int slot = 0;                                 // staging buffer of the next call
     cudaStream_t cap_stream = nullptr;
     std::vector<GraphEntry> graphs;
     std::unordered_map<MapKey, CUtensorMap, MapKeyHash> maps;
-    std::vector<BatchItem> items;
-    std::vector<int32_t> first;
+    Plan plan;                                    // the latest call's plan (vectors reused)
 };
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -115,18 +129,28 @@ static double px_weight(int variant)
     return w[variant];
 }
 
-static jdec_status ensure_host(BatchState *b, size_t need)
+static jdec_status ensure_host(BatchState *b, int k, size_t need)
 {
-    if (b->h_cap >= need) return JDEC_OK;
-    if (b->h_buf) cudaFreeHost(b->h_buf);
-    b->h_buf = nullptr;
-    b->h_cap = 0;
-    if (cudaMallocHost(&b->h_buf, need) != cudaSuccess) {
+    if (b->h_cap[k] >= need) return JDEC_OK;
+    if (b->h_buf[k]) cudaFreeHost(b->h_buf[k]);
+    b->h_buf[k] = nullptr;
+    b->h_cap[k] = 0;
+    if (cudaMallocHost(&b->h_buf[k], need) != cudaSuccess) {
         cudaGetLastError();
         return JDEC_ENOMEM;
     }
-    b->h_cap = need;
+    b->h_cap[k] = need;
     return JDEC_OK;
+}
+
+// Waits until staging buffer k (and the launches that followed its copy) has
+// been consumed.
+static void wait_slot(BatchState *b, int k)
+{
+    if (b->copy_pending[k]) {
+        cudaEventSynchronize(b->copied[k]);
+        b->copy_pending[k] = false;
+    }
 }
 
 static void drop_graphs(BatchState *b)
@@ -135,39 +159,52 @@ static void drop_graphs(BatchState *b)
     b->graphs.clear();
 }
 
-jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStream_t s)
-{
-    std::vector<Geometry> geo(n);
-    for (int i = 0; i < n; ++i) {
-        jdec_status st = validate(&imgs[i], &geo[i], false);
-        if (st != JDEC_OK) return st;
-    }
-    if (!ctx->batch) {
-        ctx->batch = new (std::nothrow) BatchState();
-        if (!ctx->batch) return JDEC_ENOMEM;
-        if (cudaEventCreateWithFlags(&ctx->batch->copied, cudaEventDisableTiming) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&ctx->batch->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
-            release_batch(ctx);   // a later call starts over instead of using half-made state
-            return JDEC_ECUDA;
-        }
-    }
-    BatchState *b = ctx->batch;
 
-    // ---- per-image strip width, variant class, and per class the union of
-    // its images' shared-memory layouts
-    std::vector<int> wt(n), var(n), cls_of(n);
+// Size class of each class's average image in the batch (the key of its
+// batch tune entry); -1 for classes not present.
+static void class_size_classes(const jdec_image *imgs, const Geometry *geo, int n, int sc[kClasses])
+{
+    long mcus[kClasses] = {0}, cnt[kClasses] = {0};
+    for (int i = 0; i < n; ++i) {
+        const int c = kQModes * variant_of(geo[i]) + qmode_of(&imgs[i], geo[i]);
+        mcus[c] += static_cast<long>(geo[i].mcus_x) * geo[i].mcus_y;
+        cnt[c] += 1;
+    }
+    for (int c = 0; c < kClasses; ++c) sc[c] = cnt[c] ? size_class_of_mcus(mcus[c] / cnt[c]) : -1;
+}
+
+// Builds the plan of the images of class `only_cls` (all classes when < 0).
+// force_wt / force_ni > 0 override the strip width and IDCT threads of the
+// planned classes (the tuner's candidates); otherwise a batch tune entry for
+// (class, size class) gives them, else the single-image table's width, else
+// the defaults (equal strips no wider than the variant's default, 64 IDCT
+// threads).
+static jdec_status build_plan(jdec_ctx *ctx, const jdec_image *imgs, const Geometry *geo, int n, int only_cls,
+                              int force_wt, int force_ni, Plan &P)
+{
+    int sc[kClasses];
+    class_size_classes(imgs, geo, n, sc);
+    P.wt.assign(n, 0);
+    P.var.assign(n, 0);
+    P.cls_of.assign(n, 0);
     UnionLayout U[kClasses];
     memset(U, 0, sizeof(U));
+    for (int c = 0; c < kClasses; ++c) {
+        const TuneEntry *t = sc[c] >= 0 ? tuned_batch(ctx, c, sc[c]) : nullptr;
+        P.nidct[c] = force_ni > 0 ? force_ni : (t && t->nidct > 0 ? t->nidct : 64);
+    }
     for (int i = 0; i < n; ++i) {
         const Geometry &g = geo[i];
-        int w = tuned_wt(ctx, g);
-        wt[i] = std::max(1, std::min(w > 0 ? w : equal_strips(g.mcus_x, default_wt(g)), kMaxWT));
-        var[i] = variant_of(g);
-        cls_of[i] = kQModes * var[i] + qmode_of(&imgs[i], g);
-        UnionLayout &u = U[cls_of[i]];
+        P.var[i] = variant_of(g);
+        P.cls_of[i] = kQModes * P.var[i] + qmode_of(&imgs[i], g);
+        const TuneEntry *t = tuned_batch(ctx, P.cls_of[i], sc[P.cls_of[i]]);
+        int w = force_wt > 0 ? force_wt : (t ? t->wt : tuned_wt(ctx, g));
+        if (w <= 0) w = default_wt(g);
+        P.wt[i] = std::max(1, std::min(equal_strips(g.mcus_x, std::min(w, kMaxWT)), kMaxWT));
+        UnionLayout &u = U[P.cls_of[i]];
         // one variant per class launch: its own number of chroma slots
         u.nslot = default_slots(g.hm, g.vm, g.fancy);
-        const SmemLayout L = smem_layout(g.hm, g.vm, g.fancy, wt[i], u.nslot);
+        const SmemLayout L = smem_layout(g.hm, g.vm, g.fancy, P.wt[i], u.nslot);
         u.stage_bytes = std::max(u.stage_bytes, L.stage_bytes);
         u.ybytes = std::max(u.ybytes, L.ybytes);
         u.slot_bytes = std::max(u.slot_bytes, L.slot_bytes);
@@ -181,28 +218,26 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
         u.off_flag = u.off_bar + 8 * kStages;
         u.total = u.off_flag + 16 + 1024;
     }
-
-    // ---- per class: cost-balanced split of its strip-rows over one wave of
-    // that class's CTAs
     struct Seg { int img, strip, rows; double row_cost; };
     std::vector<Seg> segs[kClasses];
     double total[kClasses] = {0.0};
     long rows_of[kClasses] = {0};
     for (int i = 0; i < n; ++i) {
         const Geometry &g = geo[i];
-        const int cls = cls_of[i];
-        const int ns = (g.mcus_x + wt[i] - 1) / wt[i];
+        const int cls = P.cls_of[i];
+        if (only_cls >= 0 && cls != only_cls) continue;
+        const int ns = (g.mcus_x + P.wt[i] - 1) / P.wt[i];
         for (int st = 0; st < ns; ++st) {
-            const int w = std::min(wt[i], g.mcus_x - st * wt[i]);
-            const double rc = 64.0 * g.hm * g.vm * w * px_weight(var[i]);
+            const int w = std::min(P.wt[i], g.mcus_x - st * P.wt[i]);
+            const double rc = 64.0 * g.hm * g.vm * w * px_weight(P.var[i]);
             segs[cls].push_back(Seg{i, st, g.mcus_y, rc});
             total[cls] += rc * g.mcus_y;
             rows_of[cls] += g.mcus_y;
         }
     }
-    std::vector<ClassLaunch> launches;
-    b->items.clear();
-    b->first.clear();
+    P.launches.clear();
+    P.items.clear();
+    P.first.clear();
     for (int cls = 0; cls < kClasses; ++cls) {
         if (segs[cls].empty()) continue;
         const int smem = U[cls].total;
@@ -229,68 +264,201 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
                 if (cta < nctas - 1 && acc >= (cta + 1) * share - 0.5 * sg.row_cost) ++cta;
             }
         }
-        launches.push_back(ClassLaunch{cls, nctas, smem, b->first.size(), U[cls]});
+        P.launches.push_back(ClassLaunch{cls, nctas, smem, P.first.size(), U[cls]});
         for (int c = 0; c < nctas; ++c) {
-            b->first.push_back(static_cast<int32_t>(b->items.size()));
-            b->items.insert(b->items.end(), per_cta[c].begin(), per_cta[c].end());
+            P.first.push_back(static_cast<int32_t>(P.items.size()));
+            P.items.insert(P.items.end(), per_cta[c].begin(), per_cta[c].end());
         }
-        b->first.push_back(static_cast<int32_t>(b->items.size()));
+        P.first.push_back(static_cast<int32_t>(P.items.size()));
     }
-    const int nitems = static_cast<int>(b->items.size());
-    const size_t nfirst = b->first.size();
+    return JDEC_OK;
+}
 
-    // ---- staging layout: images | items | cta_first (fixed offsets per bucket)
+// Staging layout of a plan: images | items | cta_first (offsets bucketed so
+// that similar batches share a recorded graph).
+struct StagingLayout {
+    size_t off_items, off_first, bytes;
+};
+
+static StagingLayout staging_layout(int n, const Plan &P)
+{
     const size_t img_bytes = align_up(pow2_at_least(static_cast<size_t>(n), 16) * sizeof(BatchImage), 256);
-    const size_t item_bytes = align_up(pow2_at_least(static_cast<size_t>(nitems), 256) * sizeof(BatchItem), 256);
-    const size_t first_bytes = align_up(pow2_at_least(nfirst, 256) * sizeof(int32_t), 256);
-    const size_t off_items = img_bytes, off_first = img_bytes + item_bytes;
-    const size_t bytes = off_first + first_bytes;
+    const size_t item_bytes = align_up(pow2_at_least(P.items.size(), 256) * sizeof(BatchItem), 256);
+    const size_t first_bytes = align_up(pow2_at_least(P.first.size(), 256) * sizeof(int32_t), 256);
+    return StagingLayout{img_bytes, img_bytes + item_bytes, img_bytes + item_bytes + first_bytes};
+}
 
-    void *old_dbuf = b->d_buf;
-    if (b->d_cap < bytes && b->copy_pending) {
-        cudaEventSynchronize(b->copied);   // earlier launches may still read the device buffer
-        b->copy_pending = false;
-    }
-    jdec_status st = ensure_buffer(ctx, &b->d_buf, &b->d_cap, bytes);
-    if (b->d_buf != old_dbuf) drop_graphs(b);   // recorded graphs point at the old buffer
-    if (st != JDEC_OK) return st;
-    if (b->copy_pending) {
-        cudaEventSynchronize(b->copied);   // the previous copy still reads the staging buffer
-        b->copy_pending = false;
-    }
-    if (b->h_cap < bytes) {
-        drop_graphs(b);
-        st = ensure_host(b, bytes);
-        if (st != JDEC_OK) return st;
-    }
-    uint8_t *h = static_cast<uint8_t *>(b->h_buf);
+// Writes the per-image descriptors (tensor maps, geometry, tables) and the
+// plan's work list into the staging buffer h.
+static jdec_status write_staging(BatchState *b, const jdec_image *imgs, const Geometry *geo, int n, const Plan &P,
+                                 const StagingLayout &SL, uint8_t *h)
+{
     BatchImage *hi = reinterpret_cast<BatchImage *>(h);
     for (int i = 0; i < n; ++i) {
         const Geometry &g = geo[i];
+        const int wt = P.wt[i];
         BatchImage &bi = hi[i];
         memset(&bi, 0, sizeof(bi));
         const int halo = chroma_halo(g.hm, g.fancy);
-        if (!cached_map(b, &bi.tmap[0], imgs[i].coef[0], imgs[i].blocks_w[0], imgs[i].blocks_h[0], g.hm * wt[i], g.vm))
+        if (!cached_map(b, &bi.tmap[0], imgs[i].coef[0], imgs[i].blocks_w[0], imgs[i].blocks_h[0], g.hm * wt, g.vm))
             return JDEC_ECUDA;
         for (int c = 1; c < 3; ++c) {
             // grayscale: zero chroma tiles (see zero_plane)
-            const bool ok = g.gray ? cached_map(b, &bi.tmap[c], zero_plane(), kZeroPlaneBlocks, 1, wt[i], 1)
+            const bool ok = g.gray ? cached_map(b, &bi.tmap[c], zero_plane(), kZeroPlaneBlocks, 1, wt, 1)
                                    : cached_map(b, &bi.tmap[c], imgs[i].coef[c], imgs[i].blocks_w[c],
-                                                imgs[i].blocks_h[c], wt[i] + 2 * halo, 1);
+                                                imgs[i].blocks_h[c], wt + 2 * halo, 1);
             if (!ok) return JDEC_ECUDA;
         }
-        fill_desc(&bi.desc, &imgs[i], g, wt[i], 1);
+        fill_desc(&bi.desc, &imgs[i], g, wt, 1);
         bi.desc.nslot = default_slots(g.hm, g.vm, g.fancy);
-        bi.desc.nidct = 64;
-        bi.variant = var[i];
+        bi.desc.nidct = P.nidct[P.cls_of[i]];
+        bi.variant = P.var[i];
     }
-    memcpy(h + off_items, b->items.data(), nitems * sizeof(BatchItem));
-    memcpy(h + off_first, b->first.data(), nfirst * sizeof(int32_t));
+    memcpy(h + SL.off_items, P.items.data(), P.items.size() * sizeof(BatchItem));
+    memcpy(h + SL.off_first, P.first.data(), P.first.size() * sizeof(int32_t));
+    return JDEC_OK;
+}
+
+static BatchParams class_params(jdec_ctx *ctx, BatchState *b, const StagingLayout &SL, const ClassLaunch &cl)
+{
+    BatchParams p;
+    p.imgs = static_cast<const BatchImage *>(b->d_buf);
+    p.items = reinterpret_cast<const BatchItem *>(static_cast<uint8_t *>(b->d_buf) + SL.off_items);
+    p.cta_first = reinterpret_cast<const int32_t *>(static_cast<uint8_t *>(b->d_buf) + SL.off_first) + cl.first_off;
+    p.U = cl.U;
+    p.err = ctx->d_err;
+    return p;
+}
+
+// Makes room for `bytes` in the device buffer and in staging buffer k (the
+// caller has made sure that neither is in use).
+static jdec_status ensure_batch_buffers(jdec_ctx *ctx, BatchState *b, int k, size_t bytes)
+{
+    void *old_dbuf = b->d_buf;
+    jdec_status st = ensure_buffer(ctx, &b->d_buf, &b->d_cap, bytes);
+    if (b->d_buf != old_dbuf) drop_graphs(b);   // recorded graphs point at the old buffer
+    if (st != JDEC_OK) return st;
+    if (b->h_cap[k] < bytes) {
+        drop_graphs(b);
+        st = ensure_host(b, k, bytes);
+    }
+    return st;
+}
+
+// Batch autotuner (jdec_options.autotune): for a class whose (class, size
+// class) key has no batch entry, times its persistent launch on this batch's
+// images of that class for every candidate strip width x IDCT-thread split
+// (four launches each, the first discarded), keeps the fastest and saves the
+// table.  Runs once per key; synchronises the stream.  The outputs are
+// rewritten with identical bytes by the batch's own launch afterwards.
+static void tune_class(jdec_ctx *ctx, BatchState *b, const jdec_image *imgs, const Geometry *geo, int n, int cls,
+                       int sc, cudaStream_t s)
+{
+    static const int cand_wt[] = {8, 12, 16, 20, 24, 31, 32};
+    static const int cand_ni[] = {32, 64, 96};
+    if (cudaStreamSynchronize(s) != cudaSuccess) return;
+    wait_slot(b, 0);
+    wait_slot(b, 1);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return;
+    }
+    int best_wt = 0, best_ni = 0;
+    float best_ms = 1e30f;
+    Plan P;
+    for (int wt : cand_wt) {
+        for (int ni : cand_ni) {
+            if (build_plan(ctx, imgs, geo, n, cls, wt, ni, P) != JDEC_OK || P.launches.size() != 1) continue;
+            const StagingLayout SL = staging_layout(n, P);
+            if (ensure_batch_buffers(ctx, b, 0, SL.bytes) != JDEC_OK) continue;
+            uint8_t *h = static_cast<uint8_t *>(b->h_buf[0]);
+            if (write_staging(b, imgs, geo, n, P, SL, h) != JDEC_OK) continue;
+            if (cudaMemcpyAsync(b->d_buf, h, SL.bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) break;
+            const ClassLaunch &cl = P.launches[0];
+            const BatchParams p = class_params(ctx, b, SL, cl);
+            float tot = 0.f;
+            bool ok = true;
+            for (int rep = 0; rep < 4 && ok; ++rep) {
+                cudaEventRecord(e0, s);
+                ok = launch_batch_class(cl.cls, p, cl.nctas, cl.smem, s) == cudaSuccess;
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tot += ms;   // the first launch warms the caches
+            }
+            if (!ok) {
+                cudaGetLastError();
+                continue;
+            }
+            if (tot < best_ms) {
+                best_ms = tot;
+                best_wt = wt;
+                best_ni = ni;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_wt > 0 && ctx->n_tune < kMaxTune) {
+        ctx->tune[ctx->n_tune++] = TuneEntry{cls, sc, best_wt, best_ni, 1};
+        save_tune_table(ctx);
+    }
+}
+
+jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStream_t s)
+{
+    std::vector<Geometry> geo(n);
+    for (int i = 0; i < n; ++i) {
+        jdec_status st = validate(&imgs[i], &geo[i], false);
+        if (st != JDEC_OK) return st;
+    }
+    if (!ctx->batch) {
+        ctx->batch = new (std::nothrow) BatchState();
+        if (!ctx->batch) return JDEC_ENOMEM;
+        if (cudaEventCreateWithFlags(&ctx->batch->copied[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->batch->copied[1], cudaEventDisableTiming) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&ctx->batch->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            release_batch(ctx);   // a later call starts over instead of using half-made state
+            return JDEC_ECUDA;
+        }
+    }
+    BatchState *b = ctx->batch;
+
+    if (ctx->opt.autotune) {
+        int sc[kClasses];
+        class_size_classes(imgs, geo.data(), n, sc);
+        for (int c = 0; c < kClasses; ++c)
+            if (sc[c] >= 0 && !tuned_batch(ctx, c, sc[c])) tune_class(ctx, b, imgs, geo.data(), n, c, sc[c], s);
+    }
+
+    Plan &P = b->plan;
+    jdec_status st = build_plan(ctx, imgs, geo.data(), n, -1, 0, 0, P);
+    if (st != JDEC_OK) return st;
+    const StagingLayout SL = staging_layout(n, P);
+
+    if (b->d_cap < SL.bytes) {
+        // earlier launches may still read the device buffer
+        wait_slot(b, 0);
+        wait_slot(b, 1);
+    }
+    // this call's staging buffer: the batch two calls back has consumed it
+    // (the device buffer itself is rewritten in stream order, after the
+    // previous batch's launches)
+    const int slot = b->slot;
+    wait_slot(b, slot);
+    st = ensure_batch_buffers(ctx, b, slot, SL.bytes);
+    if (st != JDEC_OK) return st;
+    uint8_t *h = static_cast<uint8_t *>(b->h_buf[slot]);
+    st = write_staging(b, imgs, geo.data(), n, P, SL, h);
+    if (st != JDEC_OK) return st;
 
     // ---- replay (or record) the copy + the class launches
     GraphEntry *ge = nullptr;
     for (auto &g : b->graphs)
-        if (g.copy_bytes == bytes && g.off_items == off_items && g.launches == launches) {
+        if (g.slot == slot && g.copy_bytes == SL.bytes && g.off_items == SL.off_items && g.launches == P.launches) {
             ge = &g;
             break;
         }
@@ -298,17 +466,11 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
         if (b->graphs.size() >= 64) drop_graphs(b);
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return JDEC_ECUDA;
-        cudaError_t e1 = cudaMemcpyAsync(b->d_buf, b->h_buf, bytes, cudaMemcpyHostToDevice, b->cap_stream);
+        cudaError_t e1 = cudaMemcpyAsync(b->d_buf, b->h_buf[slot], SL.bytes, cudaMemcpyHostToDevice, b->cap_stream);
         cudaError_t e2 = cudaSuccess;
-        for (const ClassLaunch &cl : launches) {
-            BatchParams p;
-            p.imgs = static_cast<const BatchImage *>(b->d_buf);
-            p.items = reinterpret_cast<const BatchItem *>(static_cast<uint8_t *>(b->d_buf) + off_items);
-            p.cta_first = reinterpret_cast<const int32_t *>(static_cast<uint8_t *>(b->d_buf) + off_first) + cl.first_off;
-            p.U = cl.U;
-            p.err = ctx->d_err;
-            if (e2 == cudaSuccess) e2 = launch_batch_class(cl.cls, p, cl.nctas, cl.smem, b->cap_stream);
-        }
+        for (const ClassLaunch &cl : P.launches)
+            if (e2 == cudaSuccess)
+                e2 = launch_batch_class(cl.cls, class_params(ctx, b, SL, cl), cl.nctas, cl.smem, b->cap_stream);
         cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &graph);
         if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || !graph) {
             if (graph) cudaGraphDestroy(graph);
@@ -322,12 +484,13 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
             cudaGetLastError();
             return JDEC_ECUDA;
         }
-        b->graphs.push_back(GraphEntry{bytes, off_items, launches, exec});
+        b->graphs.push_back(GraphEntry{slot, SL.bytes, SL.off_items, P.launches, exec});
         ge = &b->graphs.back();
     }
     if (cudaGraphLaunch(ge->exec, s) != cudaSuccess) return JDEC_ECUDA;
-    if (cudaEventRecord(b->copied, s) == cudaSuccess) b->copy_pending = true;
-    ctx->launches += static_cast<long>(launches.size());
+    if (cudaEventRecord(b->copied[slot], s) == cudaSuccess) b->copy_pending[slot] = true;
+    b->slot = slot ^ 1;
+    ctx->launches += static_cast<long>(P.launches.size());
     return JDEC_OK;
 }
 
@@ -335,12 +498,15 @@ void release_batch(jdec_ctx *ctx)
 {
     BatchState *b = ctx->batch;
     if (!b) return;
-    if (b->copy_pending) cudaEventSynchronize(b->copied);
+    wait_slot(b, 0);
+    wait_slot(b, 1);
     drop_graphs(b);
     if (b->d_buf) cudaFree(b->d_buf);
     ctx->owned_bytes -= b->d_cap;
-    if (b->h_buf) cudaFreeHost(b->h_buf);
-    if (b->copied) cudaEventDestroy(b->copied);
+    for (int k = 0; k < 2; ++k) {
+        if (b->h_buf[k]) cudaFreeHost(b->h_buf[k]);
+        if (b->copied[k]) cudaEventDestroy(b->copied[k]);
+    }
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;
     ctx->batch = nullptr;

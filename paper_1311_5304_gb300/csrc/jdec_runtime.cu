@@ -22,19 +22,28 @@ int variant_of(const Geometry &g)
     return g.fancy ? 4 : 3;
 }
 
-int size_class_of(const Geometry &g)
+int size_class_of_mcus(long mcus)
 {
-    const long mcus = static_cast<long>(g.mcus_x) * g.mcus_y;
     int c = 0;
     while ((1L << (c + 1)) <= mcus && c < 40) ++c;
     return c / 2;   // buckets of 4x in MCU count
 }
 
+int size_class_of(const Geometry &g) { return size_class_of_mcus(static_cast<long>(g.mcus_x) * g.mcus_y); }
+
 static const TuneEntry *tuned(jdec_ctx *ctx, const Geometry &g)
 {
     const int v = variant_of(g), sc = size_class_of(g);
     for (int i = 0; i < ctx->n_tune; ++i)
-        if (ctx->tune[i].variant == v && ctx->tune[i].size_class == sc) return &ctx->tune[i];
+        if (ctx->tune[i].kind == 0 && ctx->tune[i].variant == v && ctx->tune[i].size_class == sc) return &ctx->tune[i];
+    return nullptr;
+}
+
+const TuneEntry *tuned_batch(jdec_ctx *ctx, int cls, int size_class)
+{
+    for (int i = 0; i < ctx->n_tune; ++i)
+        if (ctx->tune[i].kind == 1 && ctx->tune[i].variant == cls && ctx->tune[i].size_class == size_class)
+            return &ctx->tune[i];
     return nullptr;
 }
 
@@ -57,8 +66,9 @@ static const char *tune_path(jdec_ctx *ctx)
     return (e && e[0]) ? e : nullptr;
 }
 
-// Table format: {"gpu": "<name>", "sms": N, "entries": [[variant, size_class, wt, idct_threads], ...]}
-// (idct_threads may be omitted or 0: default split)
+// Table format: {"gpu": "<name>", "sms": N, "entries": [[variant, size_class, wt, idct_threads, kind], ...]}
+// (idct_threads may be omitted or 0: default split; kind may be omitted: 0,
+// single-image entry; 1: batch-class entry, whose first field is the class)
 void load_tune_table(jdec_ctx *ctx)
 {
     const char *path = tune_path(ctx);
@@ -78,14 +88,16 @@ void load_tune_table(jdec_ctx *ctx)
     p = strchr(p, '[');
     if (!p) return;
     ++p;
-    while (ctx->n_tune < 64) {
+    while (ctx->n_tune < kMaxTune) {
         const char *q = strchr(p, '[');
         if (!q) break;
-        int v = 0, sc = 0, wt = 0, ni = 0;
-        const int got = sscanf(q, "[ %d , %d , %d , %d", &v, &sc, &wt, &ni);
+        int v = 0, sc = 0, wt = 0, ni = 0, kind = 0;
+        const int got = sscanf(q, "[ %d , %d , %d , %d , %d", &v, &sc, &wt, &ni, &kind);
         if (got < 3) break;
         if (got < 4 || (ni != 32 && ni != 64 && ni != 96)) ni = 0;
-        if (wt >= 1 && wt <= kMaxWT) ctx->tune[ctx->n_tune++] = TuneEntry{v, sc, wt, ni};
+        if (got < 5 || (kind != 0 && kind != 1)) kind = 0;
+        const bool ok_key = kind == 0 ? (v >= 0 && v < kVariants) : (v >= 0 && v < kClasses);
+        if (wt >= 1 && wt <= kMaxWT && ok_key) ctx->tune[ctx->n_tune++] = TuneEntry{v, sc, wt, ni, kind};
         p = strchr(q, ']');
         if (!p) break;
         ++p;
@@ -102,8 +114,8 @@ void save_tune_table(jdec_ctx *ctx)
     if (!f) return;
     fprintf(f, "{\"gpu\": \"%s\", \"sms\": %d, \"entries\": [", prop.name, ctx->sms);
     for (int i = 0; i < ctx->n_tune; ++i)
-        fprintf(f, "%s[%d, %d, %d, %d]", i ? ", " : "", ctx->tune[i].variant, ctx->tune[i].size_class, ctx->tune[i].wt,
-                ctx->tune[i].nidct);
+        fprintf(f, "%s[%d, %d, %d, %d, %d]", i ? ", " : "", ctx->tune[i].variant, ctx->tune[i].size_class,
+                ctx->tune[i].wt, ctx->tune[i].nidct, ctx->tune[i].kind);
     fprintf(f, "]}\n");
     fclose(f);
 }
@@ -113,7 +125,7 @@ void save_tune_table(jdec_ctx *ctx)
 // class.  Runs once per (variant, size class); synchronises the stream.
 void autotune_shape(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cudaStream_t s)
 {
-    if (tuned_wt(ctx, g) > 0 || ctx->n_tune >= 64) return;
+    if (tuned_wt(ctx, g) > 0 || ctx->n_tune >= kMaxTune) return;
     // the defaults (20/21, 31/32) fill whole rounds of the IDCT threads
     static const int cand[] = {4, 6, 8, 10, 12, 16, 20, 21, 24, 31, 32, 42};
     cudaEvent_t e0, e1;
@@ -139,7 +151,7 @@ void autotune_shape(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cud
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best > 0) {
-        ctx->tune[ctx->n_tune++] = TuneEntry{variant_of(g), size_class_of(g), best, 0};
+        ctx->tune[ctx->n_tune++] = TuneEntry{variant_of(g), size_class_of(g), best, 0, 0};
         save_tune_table(ctx);
     }
 }

@@ -23,15 +23,21 @@ struct Geometry {
     int64_t coef_bytes, rgb_bytes;
 };
 
-// Autotuned strip width per (variant, size class).
+// Autotuned tile shape.  kind 0: single-image launches, keyed by (variant,
+// size class of the image); kind 1: batched launches, keyed by (batch class =
+// 3 * variant + dequantisation/IDCT mode, size class of the class's average
+// image in the batch).
 struct TuneEntry {
-    int variant;     // 0: 4:4:4, 1/2: 4:2:2, 3/4: 4:2:0, 5/6: 4:4:0 (replicate / triangular)
+    int variant;     // kind 0: 0: 4:4:4, 1/2: 4:2:2, 3/4: 4:2:0, 5/6: 4:4:0 (replicate / triangular); kind 1: class
     int size_class;  // log2 of the MCU count, bucketed
     int wt;
-    int nidct;       // IDCT threads (0: default split)
+    int nidct;       // IDCT threads of split roles (0: default)
+    int kind = 0;
 };
 
 struct BatchState;
+
+constexpr int kMaxTune = 128;   // tune-table entries a context holds
 
 }  // namespace jdec
 
@@ -48,7 +54,7 @@ struct jdec_ctx {
     int occ_val[32];
     int n_occ = 0;
     // tune table
-    jdec::TuneEntry tune[64];
+    jdec::TuneEntry tune[128];
     int n_tune = 0;
     // host-buffer path: device staging
     // device staging of the host-buffer calls: two slots, so that consecutive
@@ -100,6 +106,8 @@ int equal_strips(int mcus_x, int w);   // widest equal strips no wider than w
 int size_class_of(const Geometry &g);
 int tuned_wt(jdec_ctx *ctx, const Geometry &g);
 int tuned_nidct(jdec_ctx *ctx, const Geometry &g);
+const TuneEntry *tuned_batch(jdec_ctx *ctx, int cls, int size_class);
+int size_class_of_mcus(long mcus);
 void load_tune_table(jdec_ctx *ctx);
 void save_tune_table(jdec_ctx *ctx);
 void autotune_shape(jdec_ctx *ctx, const jdec_image *img, const Geometry &g, cudaStream_t s);

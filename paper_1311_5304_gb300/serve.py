@@ -7,8 +7,11 @@ coefficient planes).  The server
   native decoder; the sequential stage of Sec. 2 stays on the CPU) into
   page-locked host planes;
 * admits decoded requests in arrival order while their device footprint
-  (coefficient planes + RGB output) fits the HBM budget; admission copies the
-  planes to the device on a copy stream;
+  (coefficient planes + RGB output) fits the HBM budget: the budget is one
+  device arena, reserved when the server starts and handed out as a ring in
+  admission order (requests retire in that order too), so admission allocates
+  nothing; it copies the planes into the request's arena region on a copy
+  stream;
 * whenever fewer than ``max_inflight`` batches are on the GPU, launches one
   batched decode (``jdec_decode_batch``: one persistent launch, CUDA graph)
   over every admitted request not yet launched, on the compute stream, after
@@ -16,6 +19,11 @@ coefficient planes).  The server
 * retires finished batches: records each request's latency from arrival to
   the batch's completion event (RGB ready in device memory) and releases its
   budget.
+
+With ``plain=True`` the same server decodes each admitted request with its
+own ``jdec_decode_coeffs`` launch as soon as its copy is issued (no batching,
+no cap on launches in flight): the per-image mode that batching is compared
+with.
 
 Host decoding of new requests overlaps GPU work on earlier ones, and requests
 that arrive while others are on the GPU join the next batch as slots and
@@ -48,28 +56,79 @@ class Request:
     qtabs: list = field(default_factory=list)
     host_planes: list = field(default_factory=list)
     host_buf: object = None              # the planes' single page-locked buffer (planes are views)
-    dev_buf: object = None               # its device copy
-    dev_planes: list = field(default_factory=list)
-    rgb: object = None                   # device RGB (H, W, 3) uint8
+    desc: object = None                  # jdec_image template (pointers filled at launch)
+    keep: list = field(default_factory=list)
+    coef_bytes: int = 0
+    plane_offs: tuple = ()               # byte offset of each plane in the request's region
+    offset: int = -1                     # the request's region in the arena (-1: none)
+    rgb: object = None                   # device RGB (H, W, 3) uint8 (kept results only)
     dev_bytes: int = 0
     copy_event: object = None
     done_time: float = 0.0
     error: str | None = None
 
 
+def _align(n: int, a: int = 256) -> int:
+    return (n + a - 1) // a * a
+
+
+class ArenaRing:
+    """Regions of one device arena handed out in FIFO order: allocations are
+    released in the order they were made, so the free space is at most two
+    runs (after the newest region, and before the oldest one)."""
+
+    def __init__(self, size: int):
+        self.size = int(size)
+        self.live = collections.deque()   # (start, end) in allocation order
+        self.used = 0
+
+    def alloc(self, n: int) -> int:
+        """Start offset of a region of n bytes (256-byte aligned), or -1."""
+        n = _align(n)
+        if n > self.size:
+            return -1
+        if not self.live:
+            start = 0
+        else:
+            first, head = self.live[0][0], self.live[-1][1]
+            if self.live[-1][0] >= first:          # not wrapped: free = [head, size) + [0, first)
+                if head + n <= self.size:
+                    start = head
+                elif n <= first:
+                    start = 0
+                else:
+                    return -1
+            elif head + n <= first:                # wrapped: free = [head, first)
+                start = head
+            else:
+                return -1
+        self.live.append((start, start + n))
+        self.used += n
+        return start
+
+    def release_oldest(self) -> None:
+        a, b = self.live.popleft()
+        self.used -= b - a
+
+
 class Server:
     def __init__(self, ctx: jdec.Context, device: int = 0, hbm_budget_bytes: int = 8 << 30,
                  workers: int | None = None, max_inflight: int = 2, max_batch: int = 1024,
-                 keep_results: bool = False):
+                 keep_results: bool = False, plain: bool = False):
         import torch
         self.torch = torch
         self.ctx = ctx
         self.dev = torch.device("cuda", device)
         self.budget = int(hbm_budget_bytes)
-        self.used = 0
+        # the budget, reserved once: every admitted request's planes and RGB
+        # live in it (no device allocation per request)
+        self.arena = torch.empty(self.budget, dtype=torch.uint8, device=self.dev)
+        self.arena_ptr = self.arena.data_ptr()
+        self.ring = ArenaRing(self.budget)
         self.max_inflight = max_inflight
         self.max_batch = max_batch
         self.keep = keep_results
+        self.plain = plain
         nthr = workers or max(1, (len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
                                   else (os.cpu_count() or 2)) - 1)
         self.pool = cf.ThreadPoolExecutor(max_workers=nthr)
@@ -79,14 +138,19 @@ class Server:
         self.decoding = collections.deque()      # (req, future) in arrival order
         self.ready = collections.deque()         # host-decoded, waiting for admission
         self.admitted = []                       # on device (copy issued), not launched
-        self.inflight = collections.deque()      # (event, [req])
+        self.inflight = collections.deque()      # (event, [req], keep)
         self.finished = []
         self.peak_used = 0
+        self._templates = {}                     # descriptor templates (see _describe)
         # device clock reference for completion times
         self.t0_event = torch.cuda.Event(enable_timing=True)
         self.t0_event.record(self.comp_stream)
         self.comp_stream.synchronize()
         self.t0_host = time.perf_counter()
+
+    @property
+    def used(self) -> int:
+        return self.ring.used
 
     # ---- host side ------------------------------------------------------------
     @staticmethod
@@ -99,6 +163,32 @@ class Server:
             off += n
         return views
 
+    def _describe(self, req: Request) -> None:
+        """Request geometry, its arena footprint and a descriptor whose
+        pointers are filled in at launch.  Descriptors are copied from
+        templates cached by geometry and quantisation tables (requests of one
+        size class and quality share one)."""
+        shapes = tuple((int(p.shape[0]), int(p.shape[1])) for p in req.host_planes)
+        key = (req.width, req.height, str(req.sampling), req.fancy, shapes,
+               b"".join(np.ascontiguousarray(q, np.uint16).tobytes() for q in req.qtabs))
+        hit = self._templates.get(key)
+        if hit is None:
+            offs, off = [], 0
+            for bh, bw in shapes:
+                offs.append(off)
+                off += bh * bw * 128
+            keep = []
+            tmpl = jdec.make_image_flat(req.width, req.height, req.sampling, 0, shapes, req.qtabs, 0,
+                                        3 * req.width, fancy=req.fancy, keep=keep)
+            coef_bytes = _align(off)
+            hit = (tmpl, keep, tuple(offs), coef_bytes, _align(coef_bytes + 3 * req.width * req.height))
+            if len(self._templates) >= 4096:
+                self._templates.clear()
+            self._templates[key] = hit
+        tmpl, keep, req.plane_offs, req.coef_bytes, req.dev_bytes = hit
+        req.keep = keep                    # the template's quantisation tables
+        req.desc = type(tmpl).from_buffer_copy(tmpl)
+
     def _host_decode(self, req: Request) -> Request:
         torch = self.torch
         if req.coefs is not None:
@@ -106,8 +196,17 @@ class Server:
             req.width, req.height = im.width, im.height
             req.sampling = (im.h_samp, im.v_samp)
             req.qtabs = im.qtabs
-            req.host_planes = im.planes          # already page-locked (torch) or numpy
-            req.host_buf = getattr(im, "host_buf", None)
+            buf = getattr(im, "host_buf", None)
+            if buf is None:
+                # stage numpy planes in one page-locked buffer
+                buf = torch.empty(sum(p.size for p in im.planes), dtype=torch.int16, pin_memory=True)
+                for v, p in zip(self._plane_views(buf, [p.shape[:2] for p in im.planes]), im.planes):
+                    v.copy_(torch.from_numpy(np.ascontiguousarray(p)))
+                req.host_planes = self._plane_views(buf, [p.shape[:2] for p in im.planes])
+            else:
+                req.host_planes = im.planes          # views of host_buf already
+            req.host_buf = buf
+            self._describe(req)
             return req
         info = jdec.jpeg_parse(req.data)
         req.width, req.height = info.width, info.height
@@ -118,6 +217,7 @@ class Server:
         planes = self._plane_views(req.host_buf, shapes)
         jdec.entropy_decode(req.data, planes)
         req.host_planes = planes
+        self._describe(req)
         return req
 
     def submit(self, req: Request) -> None:
@@ -130,11 +230,11 @@ class Server:
 
     @staticmethod
     def footprint(req: Request) -> int:
-        return sum(p.shape[0] * p.shape[1] * 128 for p in req.host_planes) + 3 * req.width * req.height
+        """Device bytes of a described request: planes + RGB, 256-byte aligned."""
+        return req.dev_bytes
 
     # ---- scheduler steps ------------------------------------------------------
     def _ready_or_reject(self, req: Request):
-        req.dev_bytes = self.footprint(req)
         if req.dev_bytes > self.budget:
             req.error = "request larger than the HBM budget"
             self.finished.append(req)
@@ -152,61 +252,86 @@ class Server:
                 self.finished.append(req)
 
     def _admit(self):
+        """Admits ready requests in arrival order while the arena has room;
+        one copy per request into its region, one event per call."""
         torch = self.torch
+        admitted = []
         with torch.cuda.stream(self.copy_stream):
-            while self.ready and self.used + self.ready[0].dev_bytes <= self.budget:
-                req = self.ready.popleft()
-                self.used += req.dev_bytes
-                self.peak_used = max(self.peak_used, self.used)
-                if req.host_buf is not None:
-                    # one copy for all planes (descriptors point into it)
-                    req.dev_buf = req.host_buf.to(self.dev, non_blocking=True)
-                else:
-                    req.dev_planes = [p.to(self.dev, non_blocking=True) if isinstance(p, torch.Tensor)
-                                      else torch.from_numpy(np.ascontiguousarray(p)).to(self.dev, non_blocking=True)
-                                      for p in req.host_planes]
-                req.rgb = torch.empty((req.height, req.width, 3), dtype=torch.uint8, device=self.dev)
-                req.copy_event = torch.cuda.Event()
-                req.copy_event.record(self.copy_stream)
-                self.admitted.append(req)
+            while self.ready:
+                req = self.ready[0]
+                off = self.ring.alloc(req.dev_bytes)
+                if off < 0:
+                    break
+                self.ready.popleft()
+                req.offset = off
+                src = req.host_buf.view(torch.uint8)
+                self.arena[off:off + src.numel()].copy_(src, non_blocking=True)
+                admitted.append(req)
+        if admitted:
+            self.peak_used = max(self.peak_used, self.ring.used)
+            ev = torch.cuda.Event()
+            ev.record(self.copy_stream)
+            for req in admitted:
+                req.copy_event = ev
+            self.admitted.extend(admitted)
+
+    def _fill(self, req: Request):
+        """The request's descriptor with its arena addresses."""
+        d = req.desc
+        base = self.arena_ptr + req.offset
+        for c, o in enumerate(req.plane_offs):
+            d.coef[c] = base + o
+        d.rgb = base + req.coef_bytes
+        return d
+
+    def _launch_plain(self):
+        # one launch per request, in admission order, each after its own copy
+        torch = self.torch
+        batch, self.admitted = self.admitted, []
+        last = None
+        for r in batch:
+            if r.copy_event is not last:
+                self.comp_stream.wait_event(r.copy_event)
+                last = r.copy_event
+            self.ctx.decode_coeffs(self._fill(r), self.comp_stream)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(self.comp_stream)
+            self.inflight.append((ev, [r]))
 
     def _launch(self):
-        if not self.admitted or len(self.inflight) >= self.max_inflight:
+        if not self.admitted:
+            return
+        if self.plain:
+            self._launch_plain()
+            return
+        if len(self.inflight) >= self.max_inflight:
             return
         torch = self.torch
         batch, self.admitted = self.admitted[:self.max_batch], self.admitted[self.max_batch:]
-        keep = []
-        descs = [jdec.make_image_flat(r.width, r.height, r.sampling, r.dev_buf.data_ptr(),
-                                      [p.shape[:2] for p in r.host_planes], r.qtabs, r.rgb.data_ptr(),
-                                      3 * r.width, fancy=r.fancy, keep=keep) if r.dev_buf is not None else
-                 jdec.make_image(r.width, r.height, r.sampling, r.dev_planes, r.qtabs, r.rgb, fancy=r.fancy,
-                                 keep=keep) for r in batch]
-        for r in batch:
-            self.comp_stream.wait_event(r.copy_event)
-            if r.dev_buf is not None:
-                r.dev_buf.record_stream(self.comp_stream)
-            else:
-                for p in r.dev_planes:
-                    p.record_stream(self.comp_stream)
-            r.rgb.record_stream(self.comp_stream)
-        self.ctx.decode_batch(descs, self.comp_stream)
+        # copies run in order on one stream: the newest event covers them all
+        self.comp_stream.wait_event(batch[-1].copy_event)
+        self.ctx.decode_batch([self._fill(r) for r in batch], self.comp_stream)
         ev = torch.cuda.Event(enable_timing=True)
         ev.record(self.comp_stream)
-        self.inflight.append((ev, batch, keep))
+        self.inflight.append((ev, batch))
 
     def _retire(self):
         while self.inflight and self.inflight[0][0].query():
-            ev, batch, _ = self.inflight.popleft()
+            ev, batch = self.inflight.popleft()
             done = self.t0_host + self.t0_event.elapsed_time(ev) / 1e3
             for r in batch:
                 r.done_time = done
-                self.used -= r.dev_bytes
-                r.dev_planes = []
-                r.dev_buf = None
+                if self.keep:
+                    # copied out on the copy stream, so that later copies into
+                    # the released region are ordered after it
+                    n = 3 * r.width * r.height
+                    o = r.offset + r.coef_bytes
+                    with self.torch.cuda.stream(self.copy_stream):
+                        r.rgb = self.arena[o:o + n].view(r.height, r.width, 3).clone()
+                self.ring.release_oldest()
+                r.offset = -1
                 r.host_planes = []
                 r.host_buf = None
-                if not self.keep:
-                    r.rgb = None
                 self.finished.append(r)
 
     def step(self):
@@ -230,6 +355,9 @@ class Server:
     def close(self):
         self.pool.shutdown(wait=True)
         self.ctx.sync(self.comp_stream, check=False)
+        self.comp_stream.synchronize()
+        self.copy_stream.synchronize()
+        self.arena = None
 
 
 # ---- load generation -------------------------------------------------------------

@@ -131,3 +131,24 @@ def test_config4_full_batch_matches_oracle(ctx, orc):
         assert np.array_equal(ref.cpu().numpy(), got), i
         im = synth.batch_image(specs, atl, offs, i)
         assert_same(got, oracle_rgb(orc, im), f"config-4 image {i} {im.width}x{im.height} {s}")
+
+
+def test_back_to_back_batches_without_waiting(ctx, orc):
+    # Calls issued back to back prepare their work lists in alternating
+    # staging buffers while earlier batches still run; each batch must still
+    # decode its own images (same and different shapes, no host wait between)
+    rng = np.random.default_rng(23)
+    batches = [_mixed(rng, 9, 260, 200), None, _mixed(rng, 14, 180, 120), None, _mixed(rng, 5, 400, 300)]
+    batches[1] = [synth.random_image(rng, im.width, im.height, im.sampling, fancy=im.fancy) for im in batches[0]]
+    batches[3] = [synth.random_image(rng, im.width, im.height, im.sampling, fancy=im.fancy) for im in batches[2]]
+    keep, outs = [], []
+    for imgs in batches:
+        planes = [upload(im) for im in imgs]
+        rgbs = _rgb_buffers(imgs)
+        keep.append(planes)
+        ctx.decode_batch(_descs(imgs, planes, rgbs, keep))
+        outs.append(rgbs)
+    ctx.sync()
+    for b, imgs in enumerate(batches):
+        for i, im in enumerate(imgs):
+            assert_same(outs[b][i].cpu().numpy(), oracle_rgb(orc, im, 1), f"batch {b} image {i}")

@@ -136,3 +136,22 @@ def test_grayscale_requests_in_the_mix(ctx, orc):
     for i, (_, g) in enumerate(grays):
         want = orc.backend_decode_gray(g.width, g.height, g.planes[0], g.qtabs[0])
         assert np.array_equal(by[i].rgb.cpu().numpy(), want), i
+
+
+def test_plain_mode_gives_the_batched_results(ctx):
+    # the per-request launch mode (one jdec_decode_coeffs per request) decodes
+    # every request to the same bytes as its standalone decode
+    pool = serve.request_pool(83, per_class=(4, 3, 1), mix=MIX)
+    srv = serve.Server(ctx, hbm_budget_bytes=64 << 20, keep_results=True, plain=True)
+    try:
+        stats = serve.run_load(srv, pool, rate=4000.0, n=120, seed=6, mix=MIX, timeout=60)
+    finally:
+        srv.close()
+    assert stats["drained"] and stats["completed"] == 120 and stats["errors"] == 0
+    assert srv.peak_used <= 64 << 20
+    alone = {}
+    for r in srv.finished:
+        key = id(r.data)
+        if key not in alone:
+            alone[key] = _standalone(ctx, r.data)[0]
+        assert np.array_equal(r.rgb.cpu().numpy(), alone[key]), r.rid
