@@ -185,22 +185,42 @@ int equal_strips(int mcus_x, int w)
 // Default strip width of an image whose `nrows` MCU rows are decoded by one
 // launch of up to `wave` CTAs: narrower strips while there are too few
 // strip-rows to give every CTA a few rows (small images), then equal strips.
-static int fit_wt(const Geometry &g, int nrows, long wave)
+static bool enough_rows(const Geometry &g, int nrows, long wave, int w)
 {
     const long min_rows = (g.fancy && g.vm == 2) ? 6 : 2;
+    return static_cast<long>((g.mcus_x + w - 1) / w) * nrows >= min_rows * wave;
+}
+
+static int fit_wt(const Geometry &g, int nrows, long wave)
+{
     int w = default_wt(g);
-    while (w > 4 && static_cast<long>((g.mcus_x + w - 1) / w) * nrows < min_rows * wave) w = std::max(4, w / 2);
+    while (w > 4 && !enough_rows(g, nrows, wave, w)) w = std::max(4, w / 2);
     return equal_strips(g.mcus_x, w);
 }
 
 // Strip width (MCUs) and the number of CTAs for `nrows` MCU rows of an image:
 // one full wave (occupancy x SMs) or fewer when there are fewer strip-rows.
-void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int *wt, int *nctas, int *smem)
+// fw > 0: the variant's compile-time width; when the image is at least that
+// wide, the last strip's padding stays small and there are enough strip-rows
+// at that width (and no width is forced or tuned), every strip is fw wide
+// (the last one padded) and *fixed is set.
+void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int fw, int *wt, int *nctas, int *smem,
+                bool *fixed)
 {
     int w = force_wt > 0 ? force_wt : tuned_wt(ctx, g);
+    *fixed = false;
     if (w <= 0) {
         const SmemLayout L0 = smem_layout(g.hm, g.vm, g.fancy, default_wt(g), default_slots(g.hm, g.vm, g.fancy));
-        w = fit_wt(g, nrows, static_cast<long>(occupancy_cached(ctx, g.hm, g.vm, g.fancy, L0.total)) * ctx->sms);
+        const long wave = static_cast<long>(occupancy_cached(ctx, g.hm, g.vm, g.fancy, L0.total)) * ctx->sms;
+        // (the padded part of the last strip, decoded but not written, stays
+        // under 2 % of the width)
+        const long pad = ((g.mcus_x + fw - 1) / fw) * static_cast<long>(fw) - g.mcus_x;
+        if (fw > 0 && g.mcus_x >= fw && 50 * pad <= g.mcus_x && enough_rows(g, nrows, wave, fw)) {
+            w = fw;
+            *fixed = true;
+        } else {
+            w = fit_wt(g, nrows, wave);
+        }
     }
     w = std::max(1, std::min(w, kMaxWT));
     const SmemLayout L = smem_layout(g.hm, g.vm, g.fancy, w, default_slots(g.hm, g.vm, g.fancy));
@@ -289,12 +309,15 @@ jdec_status launch_rows(jdec_ctx *ctx, const jdec_image *img, const Geometry &g,
 {
     if (row1 <= row0) return JDEC_OK;
     int wt, nctas, smem;
-    plan_tiles(ctx, g, row1 - row0, force_wt, &wt, &nctas, &smem);
+    bool fixed;
+    const int ni = tuned_nidct(ctx, g);
+    // the compile-time-width instances run the default split (64 IDCT threads)
+    const int fw = (ni > 0 && ni != 64) ? 0 : fixed_wt(g.hm, g.vm, g.fancy, qmode_of(img, g));
+    plan_tiles(ctx, g, row1 - row0, force_wt, fw, &wt, &nctas, &smem, &fixed);
     DecodeParams p;
     memset(&p, 0, sizeof(p));
     if (!encode_maps(p.tmap, img, g, wt)) return JDEC_ECUDA;
     fill_desc(&p.img, img, g, wt, nctas);
-    const int ni = tuned_nidct(ctx, g);
     if (ni > 0) p.img.nidct = ni;
     p.img.row0 = row0;
     p.img.row1 = row1;
@@ -303,7 +326,7 @@ jdec_status launch_rows(jdec_ctx *ctx, const jdec_image *img, const Geometry &g,
     // unified roles pay off on strips of 16 MCUs or more (measured: 4:2:2 on
     // 4000x3000 +10 %, 8192x8192 and 4:2:0 unchanged; narrower strips gain nothing)
     const bool unified = g.fancy && g.hm == 2 && wt >= 16;
-    cudaError_t e = launch_fused(g.hm, g.vm, g.fancy, unified, p, grid, smem, s);
+    cudaError_t e = launch_fused(g.hm, g.vm, g.fancy, unified, fixed, p, grid, smem, s);
     if (e != cudaSuccess) return JDEC_ECUDA;
     ctx->launches++;
     return JDEC_OK;

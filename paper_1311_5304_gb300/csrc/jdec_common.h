@@ -119,6 +119,18 @@ struct SmemLayout {
 
 __host__ __device__ inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
+// Strip widths with a compile-time-width fast path in the single-image kernel
+// (the variants' default widths, 8-bit tables): 4:4:4 32 MCUs, triangular
+// 4:2:2 31, triangular 4:2:0 20; 0 = none.
+__host__ __device__ inline int fixed_wt(int hm, int vm, bool fancy, int qmode)
+{
+    if (qmode != kQ8) return 0;
+    if (hm == 1 && vm == 1) return 32;
+    if (hm == 2 && vm == 1 && fancy) return 31;
+    if (hm == 2 && vm == 2 && fancy) return 20;
+    return 0;
+}
+
 __host__ __device__ inline SmemLayout apply_union(SmemLayout L, const UnionLayout &U)
 {
     L.stage_bytes = U.stage_bytes;

@@ -152,16 +152,17 @@ __device__ __forceinline__ void idct8(const int x0, const int x1, const int x2, 
     const int a1 = (x0 - x4) * 8192 + rnd;
     const int b0 = x2 * 10703 + x6 * 4433;
     const int b1 = x2 * 4433 - x6 * 10704;
-    const int e0 = a0 + b0, e3 = a0 - b0;
-    const int e1 = a1 + b1, e2 = a1 - b1;
     const int o0 = x1 * 11363 + x3 * 9633 + x5 * 6437 + x7 * 2260;
     const int o1 = x1 * 9633 - x3 * 2259 - x5 * 11362 - x7 * 6436;
     const int o2 = x1 * 6437 - x3 * 11362 + x5 * 2261 + x7 * 9633;
     const int o3 = x1 * 2260 - x3 * 6436 + x5 * 9633 - x7 * 11363;
-    y[0] = e0 + o0; y[7] = e0 - o0;
-    y[1] = e1 + o1; y[6] = e1 - o1;
-    y[2] = e2 + o2; y[5] = e2 - o2;
-    y[3] = e3 + o3; y[4] = e3 - o3;
+    // y_n = e_n + o_n, y_{7-n} = e_n - o_n with e_0,3 = a0 +- b0 and
+    // e_1,2 = a1 +- b1, each output written as one three-term sum (no shared
+    // e_n), so that it is a single three-input add
+    y[0] = a0 + (b0 + o0); y[7] = a0 + (b0 - o0);
+    y[1] = a1 + (b1 + o1); y[6] = a1 + (b1 - o1);
+    y[2] = a1 - (b1 - o2); y[5] = a1 - (b1 + o2);
+    y[3] = a0 - (b0 - o3); y[4] = a0 - (b0 + o3);
 }
 
 __device__ __forceinline__ int sext_lo(uint32_t w) { return static_cast<int>(static_cast<int16_t>(w & 0xffffu)); }

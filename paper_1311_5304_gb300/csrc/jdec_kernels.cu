@@ -10,7 +10,9 @@
 
 namespace jdec {
 
-template <int HM, int VM, bool FANCY, int QM, bool UNI>
+// FW > 0: the launch's strip width is FW (full strips run compile-time-width
+// code, see run_share).
+template <int HM, int VM, bool FANCY, int QM, bool UNI, int FW = 0>
 __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_fused_kernel(const __grid_constant__ DecodeParams p)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -25,13 +27,13 @@ __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_fused_kernel(
     }
     __syncthreads();
     PipeState ps{0u, 0, 0};
-    run_share<HM, VM, FANCY, QM, UNI>(p.tmap, p.img, blockIdx.x, smem, L, ps, p.err, true);
+    run_share<HM, VM, FANCY, QM, UNI, FW>(p.tmap, p.img, blockIdx.x, smem, L, ps, p.err, true);
 }
 
-template <int HM, int VM, bool FANCY, int QM, bool UNI = false>
+template <int HM, int VM, bool FANCY, int QM, bool UNI = false, int FW = 0>
 static cudaError_t launch_variant(const DecodeParams &p, int grid, int smem, cudaStream_t s)
 {
-    auto k = jdec_fused_kernel<HM, VM, FANCY, QM, UNI>;
+    auto k = jdec_fused_kernel<HM, VM, FANCY, QM, UNI, FW>;
     static ConfigFlags configured;
     cudaError_t e = configure_kernel(k, configured);
     if (e != cudaSuccess) return e;
@@ -53,9 +55,22 @@ static cudaError_t launch_q(int hm, int vm, bool fancy, bool uni, const DecodePa
     return uni ? launch_variant<2, 2, true, QM, true>(p, grid, smem, s) : launch_variant<2, 2, true, QM>(p, grid, smem, s);
 }
 
-cudaError_t launch_fused(int hm, int vm, bool fancy, bool unified, const DecodeParams &p, int grid, int smem,
-                         cudaStream_t s)
+// The compile-time-width instances (see fixed_wt): split roles for 4:4:4,
+// unified roles for the triangular 4:2:2 / 4:2:0 strips.
+static cudaError_t launch_fixed(int hm, int vm, bool fancy, const DecodeParams &p, int grid, int smem,
+                                cudaStream_t s)
 {
+    if (p.img.qmode != kQ8 || p.img.wt != fixed_wt(hm, vm, fancy, kQ8)) return cudaErrorInvalidValue;
+    if (hm == 1 && vm == 1) return launch_variant<1, 1, false, kQ8, false, 32>(p, grid, smem, s);
+    if (hm == 2 && vm == 1 && fancy) return launch_variant<2, 1, true, kQ8, true, 31>(p, grid, smem, s);
+    if (hm == 2 && vm == 2 && fancy) return launch_variant<2, 2, true, kQ8, true, 20>(p, grid, smem, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fused(int hm, int vm, bool fancy, bool unified, bool fixed, const DecodeParams &p, int grid,
+                         int smem, cudaStream_t s)
+{
+    if (fixed) return launch_fixed(hm, vm, fancy, p, grid, smem, s);
     switch (p.img.qmode) {
     case kQ16: return launch_q<kQ16>(hm, vm, fancy, unified, p, grid, smem, s);
     case kQ8: return launch_q<kQ8>(hm, vm, fancy, unified, p, grid, smem, s);

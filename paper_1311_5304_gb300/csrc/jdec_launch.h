@@ -6,9 +6,11 @@
 
 namespace jdec {
 
-// unified: every warp transforms and converts (triangular 4:2:2 / 4:2:0 only)
-cudaError_t launch_fused(int hm, int vm, bool fancy, bool unified, const DecodeParams &p, int grid, int smem,
-                         cudaStream_t s);
+// unified: every warp transforms and converts (triangular 4:2:2 / 4:2:0 only);
+// fixed: the compile-time-width instance for p.img.wt == fixed_wt(...)
+// (unified roles for 4:2:2 / 4:2:0, split for 4:4:4; 64 IDCT threads)
+cudaError_t launch_fused(int hm, int vm, bool fancy, bool unified, bool fixed, const DecodeParams &p, int grid,
+                         int smem, cudaStream_t s);
 int fused_occupancy(int hm, int vm, bool fancy, int smem);
 cudaError_t launch_batch(const BatchParams &p, int grid, int smem, cudaStream_t s);
 int batch_occupancy(int smem);

@@ -84,7 +84,8 @@ const char *status_str(jdec_status s);
 bool encode_plane_map(CUtensorMap *m, const int16_t *base, int bw, int bh, int box_w, int box_h);
 // allow_test: accept the JDEC_TEST_WITHHOLD_LOADS flag (single-image launches only)
 jdec_status validate(const jdec_image *img, Geometry *g, bool host_buffers, bool allow_test = false);
-void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int *wt, int *nctas, int *smem);
+void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int fw, int *wt, int *nctas, int *smem,
+                bool *fixed);
 void fill_desc(ImageDesc *d, const jdec_image *img, const Geometry &g, int wt, int nctas);
 // Dequantisation + IDCT mode of an image: kAAN when asked for, else kQ8 when
 // every quantisation step fits in 8 bits, else kQ16.

@@ -52,6 +52,7 @@ struct PipeState {
     int sync_from;     // first job whose colour warps signal EMPTY (split roles)
 };
 
+
 template <int HM, int VM, bool FANCY>
 struct Variant {
     static constexpr bool kHalo = FANCY && HM == 2;            // horizontal neighbours
@@ -288,16 +289,121 @@ __device__ __forceinline__ void load_qtables(int *qs, const ImageDesc &d, int ti
     }
 }
 
+// One dequantisation + IDCT task (block at shared address blk -> samples at dst).
+template <int QM>
+__device__ __forceinline__ void idct_task(uint32_t blk, const int *q, uint8_t *dst, int pitch)
+{
+    if (QM == kQ8)
+        idct_block_q8(blk, reinterpret_cast<const uint32_t *>(q), dst, pitch);
+    else if (QM == kAAN)
+        idct_block_aan(blk, q, dst, pitch);
+    else
+        idct_block(blk, q, dst, pitch);
+}
+
+// The IDCT tasks of one job on threads [0, nthr) (this thread: tid), any
+// strip width: luma blocks (nye, rows of HM * wte) when has_y, then chroma
+// blocks [lb0, lb0 + nce) of both components when has_c.
 template <int HM, int VM, bool FANCY, int QM>
+__device__ __forceinline__ void idct_job(uint8_t *stage, uint8_t *yplane, uint8_t *slot, const int *qs,
+                                         const SmemLayout &L, bool has_y, bool has_c, int nye, int nce, int lb0,
+                                         int wt, int wte, int tid, int nthr)
+{
+    const int ntask = (has_y ? nye : 0) + (has_c ? 2 * nce : 0);
+    for (int t = tid; t < ntask; t += nthr) {
+        uint32_t blk;
+        const int *q;
+        uint8_t *dst;
+        int pitch;
+        int tc = t;
+        if (has_y && t < nye) {
+            const int vy = t / (HM * wte), bx = t - vy * (HM * wte);
+            blk = smem_u32(stage + L.stage_y + (vy * HM * wt + bx) * 128);
+            q = qs;
+            dst = yplane + 8 * vy * L.ypitch + 8 * bx;
+            pitch = L.ypitch;
+        } else {
+            if (has_y) tc -= nye;
+            const int comp = tc >= nce;
+            const int lb = lb0 + (comp ? tc - nce : tc);
+            blk = smem_u32(stage + L.stage_c + comp * L.cbytes + lb * 128);
+            q = qs + 64 * (1 + comp);
+            dst = slot + comp * 8 * L.lc + 8 * lb;
+            pitch = L.lc;
+        }
+        idct_task<QM>(blk, q, dst, pitch);
+    }
+}
+
+// The same for strips of exactly FW MCUs (compile-time width) on NT threads:
+// every chroma block of the TMA box is transformed, halo blocks included (at
+// the image's edges they hold zero-filled blocks, whose samples the edge
+// replication then overwrites), so the task list is the same for every job:
+// luma tasks 0 .. NY-1, chroma NY .. NY + 2 NC - 1.  Each thread's tasks
+// (t = tid + i NT) and their shared-memory offsets are worked out once.
+template <int HM, int VM, bool FANCY, int QM, int FW, int NT>
+struct FixedIdct {
+    static constexpr int kHalo = Variant<HM, VM, FANCY>::kHalo ? 1 : 0;
+    static constexpr int NY = HM * VM * FW;
+    static constexpr int NC = FW + 2 * kHalo;
+    static constexpr int NTASK = NY + 2 * NC;
+    static constexpr int NS = (NTASK + NT - 1) / NT;
+    uint32_t src[NS];   // offset of the block in a stage
+    uint32_t dst[NS];   // offset of the samples in the luma plane (luma) or the chroma slot
+    int pitch[NS];
+    int qoff[NS];
+
+    __device__ __forceinline__ void init(const SmemLayout &L, int tid)
+    {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const int t = tid + i * NT;
+            if (t < NY) {
+                const int vy = t / (HM * FW), bx = t - vy * (HM * FW);
+                src[i] = L.stage_y + 128 * t;
+                dst[i] = 8 * vy * L.ypitch + 8 * bx;
+                pitch[i] = L.ypitch;
+                qoff[i] = 0;
+            } else {
+                const int tc = t - NY;
+                const int comp = tc >= NC;
+                const int lb = comp ? tc - NC : tc;
+                src[i] = L.stage_c + comp * L.cbytes + 128 * lb;
+                dst[i] = comp * 8 * L.lc + 8 * lb;
+                pitch[i] = L.lc;
+                qoff[i] = 64 * (1 + comp);
+            }
+        }
+    }
+
+    __device__ __forceinline__ void run(uint8_t *stage, uint8_t *yplane, uint8_t *slot, const int *qs, bool has_y,
+                                        bool has_c, int tid) const
+    {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const int t = tid + i * NT;
+            if (t >= NTASK) break;
+            const bool luma = t < NY;
+            if (luma ? !has_y : !has_c) continue;
+            idct_task<QM>(smem_u32(stage + src[i]), qs + qoff[i], (luma ? yplane : slot) + dst[i], pitch[i]);
+        }
+    }
+};
+
+// FW > 0: the strip is decoded as exactly FW MCUs wide (d.wt == FW; a last
+// strip that reaches past the image's right edge is padded, see run_share), L
+// is the layout for width FW, the IDCT threads number 64: task lists and
+// offsets are compile-time (FixedIdct).  FW = 0: any strip.
+template <int HM, int VM, bool FANCY, int QM, int FW = 0>
 __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const ImageDesc &qsrc, int strip, int r0,
                                int r1, uint8_t *smem, const SmemLayout &L, PipeState &ps, int *err, bool last,
                                bool reload_q)
 {
     using V = Variant<HM, VM, FANCY>;
     const int tid = threadIdx.x;
-    const int wt = d.wt;
+    const int wt = FW ? FW : d.wt;
     const int mx0 = strip * wt;
-    const int wte = min(wt, d.mcus_x - mx0);
+    const int wte = FW ? FW : min(wt, d.mcus_x - mx0);
     if (r0 >= r1 || wte <= 0) return true;
     const int njobs = V::kPro + (r1 - r0);
     const int J0 = ps.job;
@@ -308,7 +414,7 @@ __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const Im
     const uint32_t bar0 = smem_u32(smem + L.off_bar);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L.off_flag);
 
-    const int nidct = d.nidct, ncc = kCtaThreads - d.nidct;
+    const int nidct = FW ? 64 : d.nidct, ncc = kCtaThreads - nidct;
     if (tid < nidct) {
         // =================== IDCT warps ===================
         int *qs = reinterpret_cast<int *>(smem + L.off_q);
@@ -317,13 +423,16 @@ __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const Im
             load_qtables<QM>(qs, qsrc, tid, nidct);
             named_sync(kBarIdct, nidct);
         }
-        const int lb0 = (V::kHalo && mx0 == 0) ? 1 : 0;
-        const int lb1 = min(wte + (V::kHalo ? 2 : 0), d.mcus_x - (mx0 - (V::kHalo ? 1 : 0)));
+        const int lb0 = (!FW && V::kHalo && mx0 == 0) ? 1 : 0;
+        const int lb1 = FW ? FW + (V::kHalo ? 2 : 0)
+                           : min(wte + (V::kHalo ? 2 : 0), d.mcus_x - (mx0 - (V::kHalo ? 1 : 0)));
         const int nce = lb1 - lb0;
         const int nye = VM * HM * wte;
         const int used = 8 * (wte + (V::kHalo ? 2 : 0));
         const bool edge = V::kHalo && (mx0 == 0 || d.cw + 7 - 8 * mx0 < used - 1);
         const uint64_t budget = 2000000000ull;   // 2 s per wait
+        FixedIdct<HM, VM, FANCY, QM, FW ? FW : 1, 64> fx;
+        if (FW) fx.init(L, tid);
 
         if (tid == 0) {
             fence_proxy_async_smem();
@@ -347,34 +456,12 @@ __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const Im
             uint8_t *stage = stages + s * L.stage_bytes;
             uint8_t *yplane = yplanes + s * L.ybytes;
             uint8_t *slot = cslots + (j & (L.nslot - 1)) * L.slot_bytes;
-            const int ntask = (yrow >= 0 ? nye : 0) + (do_c ? 2 * nce : 0);
-            for (int t = tid; ok && t < ntask; t += nidct) {
-                uint32_t blk;
-                const int *q;
-                uint8_t *dst;
-                int pitch;
-                int tc = t;
-                if (yrow >= 0 && t < nye) {
-                    const int vy = t / (HM * wte), bx = t - vy * (HM * wte);
-                    blk = smem_u32(stage + L.stage_y + (vy * HM * wt + bx) * 128);
-                    q = qs;
-                    dst = yplane + 8 * vy * L.ypitch + 8 * bx;
-                    pitch = L.ypitch;
-                } else {
-                    if (yrow >= 0) tc -= nye;
-                    const int comp = tc >= nce;
-                    const int lb = lb0 + (comp ? tc - nce : tc);
-                    blk = smem_u32(stage + L.stage_c + comp * L.cbytes + lb * 128);
-                    q = qs + 64 * (1 + comp);
-                    dst = slot + comp * 8 * L.lc + 8 * lb;
-                    pitch = L.lc;
-                }
-                if (QM == kQ8)
-                    idct_block_q8(blk, reinterpret_cast<const uint32_t *>(q), dst, pitch);
-                else if (QM == kAAN)
-                    idct_block_aan(blk, q, dst, pitch);
+            if (ok) {
+                if (FW)
+                    fx.run(stage, yplane, slot, qs, yrow >= 0, do_c, tid);
                 else
-                    idct_block(blk, q, dst, pitch);
+                    idct_job<HM, VM, FANCY, QM>(stage, yplane, slot, qs, L, yrow >= 0, do_c, nye, nce, lb0, wt, wte,
+                                                tid, nidct);
             }
             named_sync(kBarIdct, nidct);
             if (*abort_flag) {
@@ -455,15 +542,16 @@ __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const Im
 // the barrier of job k+1, which every thread reaches only after finishing the
 // colour tasks of job k.  No named barrier is left half-signalled, so an item
 // of either kind may follow.
-template <int HM, int VM, bool FANCY, int QM>
+// FW as for run_work_split (all 128 threads transform).
+template <int HM, int VM, bool FANCY, int QM, int FW = 0>
 __device__ bool run_work_unified(const CUtensorMap *tm, const ItemDesc d, const ImageDesc &qsrc, int strip, int r0,
                                  int r1, uint8_t *smem, const SmemLayout &L, PipeState &ps, int *err, bool reload_q)
 {
     using V = Variant<HM, VM, FANCY>;
     const int tid = threadIdx.x;
-    const int wt = d.wt;
+    const int wt = FW ? FW : d.wt;
     const int mx0 = strip * wt;
-    const int wte = min(wt, d.mcus_x - mx0);
+    const int wte = FW ? FW : min(wt, d.mcus_x - mx0);
     if (r0 >= r1 || wte <= 0) return true;
     const int njobs = V::kPro + (r1 - r0);
     const int J0 = ps.job;
@@ -480,13 +568,15 @@ __device__ bool run_work_unified(const CUtensorMap *tm, const ItemDesc d, const 
         load_qtables<QM>(qs, qsrc, tid, kCtaThreads);
         __syncthreads();
     }
-    const int lb0 = (V::kHalo && mx0 == 0) ? 1 : 0;
-    const int lb1 = min(wte + (V::kHalo ? 2 : 0), d.mcus_x - (mx0 - (V::kHalo ? 1 : 0)));
+    const int lb0 = (!FW && V::kHalo && mx0 == 0) ? 1 : 0;
+    const int lb1 = FW ? FW + (V::kHalo ? 2 : 0) : min(wte + (V::kHalo ? 2 : 0), d.mcus_x - (mx0 - (V::kHalo ? 1 : 0)));
     const int nce = lb1 - lb0;
     const int nye = VM * HM * wte;
     const int used = 8 * (wte + (V::kHalo ? 2 : 0));
     const bool edge = V::kHalo && (mx0 == 0 || d.cw + 7 - 8 * mx0 < used - 1);
     const uint64_t budget = 2000000000ull;   // 2 s per wait
+    FixedIdct<HM, VM, FANCY, QM, FW ? FW : 1, kCtaThreads> fx;
+    if (FW) fx.init(L, tid);
 
     if (tid == 0) {
         // the stages were consumed before the barrier of the previous job
@@ -517,34 +607,12 @@ __device__ bool run_work_unified(const CUtensorMap *tm, const ItemDesc d, const 
         uint8_t *stage = stages + s * L.stage_bytes;
         uint8_t *yplane = yplanes + s * L.ybytes;
         uint8_t *slot = cslots + (j & (L.nslot - 1)) * L.slot_bytes;
-        const int ntask = (yrow >= 0 ? nye : 0) + (do_c ? 2 * nce : 0);
-        for (int t = tid; ok && t < ntask; t += kCtaThreads) {
-            uint32_t blk;
-            const int *q;
-            uint8_t *dst;
-            int pitch;
-            int tc = t;
-            if (yrow >= 0 && t < nye) {
-                const int vy = t / (HM * wte), bx = t - vy * (HM * wte);
-                blk = smem_u32(stage + L.stage_y + (vy * HM * wt + bx) * 128);
-                q = qs;
-                dst = yplane + 8 * vy * L.ypitch + 8 * bx;
-                pitch = L.ypitch;
-            } else {
-                if (yrow >= 0) tc -= nye;
-                const int comp = tc >= nce;
-                const int lb = lb0 + (comp ? tc - nce : tc);
-                blk = smem_u32(stage + L.stage_c + comp * L.cbytes + lb * 128);
-                q = qs + 64 * (1 + comp);
-                dst = slot + comp * 8 * L.lc + 8 * lb;
-                pitch = L.lc;
-            }
-            if (QM == kQ8)
-                idct_block_q8(blk, reinterpret_cast<const uint32_t *>(q), dst, pitch);
-            else if (QM == kAAN)
-                idct_block_aan(blk, q, dst, pitch);
+        if (ok) {
+            if (FW)
+                fx.run(stage, yplane, slot, qs, yrow >= 0, do_c, tid);
             else
-                idct_block(blk, q, dst, pitch);
+                idct_job<HM, VM, FANCY, QM>(stage, yplane, slot, qs, L, yrow >= 0, do_c, nye, nce, lb0, wt, wte, tid,
+                                            kCtaThreads);
         }
         __syncthreads();
         if (*abort_flag) {
@@ -590,14 +658,14 @@ __device__ bool run_work_unified(const CUtensorMap *tm, const ItemDesc d, const 
 // split roles (see run_work_split and run_work_unified).  `last` = this is
 // the CTA's final item, or the next item may use the other kind of roles:
 // the split version then drains its barriers.
-template <int HM, int VM, bool FANCY, int QM, bool UNI>
+template <int HM, int VM, bool FANCY, int QM, bool UNI, int FW = 0>
 __device__ __forceinline__ bool run_work(const CUtensorMap *tm, const ItemDesc d, const ImageDesc &qsrc, int strip,
                                          int r0, int r1, uint8_t *smem, const SmemLayout &L, PipeState &ps, int *err,
                                          bool last, bool reload_q)
 {
     if (UNI && Variant<HM, VM, FANCY>::kCanUnify)
-        return run_work_unified<HM, VM, FANCY, QM>(tm, d, qsrc, strip, r0, r1, smem, L, ps, err, reload_q);
-    return run_work_split<HM, VM, FANCY, QM>(tm, d, qsrc, strip, r0, r1, smem, L, ps, err, last, reload_q);
+        return run_work_unified<HM, VM, FANCY, QM, FW>(tm, d, qsrc, strip, r0, r1, smem, L, ps, err, reload_q);
+    return run_work_split<HM, VM, FANCY, QM, FW>(tm, d, qsrc, strip, r0, r1, smem, L, ps, err, last, reload_q);
 }
 
 }  // namespace jdec
@@ -606,8 +674,12 @@ namespace jdec {
 
 // Runs this CTA's share of an image: the strips' MCU rows in [row0, row1),
 // concatenated strip after strip, split evenly over `nctas` CTAs; `b` is the
-// CTA's index among them.
-template <int HM, int VM, bool FANCY, int QM, bool UNI>
+// CTA's index among them.  FW > 0 (the launch's strip width, d.wt == FW):
+// every strip runs the compile-time-width code; a last strip that reaches
+// past the image's right edge is decoded as a full one (its blocks beyond the
+// edge are zero-filled by TMA, the chroma halo is replaced by the true edge,
+// and no pixel beyond the image is written).
+template <int HM, int VM, bool FANCY, int QM, bool UNI, int FW = 0>
 __device__ bool run_share(const CUtensorMap *tm, const ImageDesc &d, int b, uint8_t *smem, const SmemLayout &L,
                           PipeState &ps, int *err, bool last_image)
 {
@@ -621,9 +693,17 @@ __device__ bool run_share(const CUtensorMap *tm, const ImageDesc &d, int b, uint
         const int rr = static_cast<int>(a - s * nrows);
         const int len = static_cast<int>(min(e - a, nrows - rr));
         a += len;
-        if (!run_work<HM, VM, FANCY, QM, UNI>(tm, id, d, s, d.row0 + rr, d.row0 + rr + len, smem, L, ps, err,
-                                         last_image && a >= e, false))
-            return false;
+        const bool last = last_image && a >= e;
+        bool ok;
+        if (FW) {
+            const SmemLayout LF = smem_layout(HM, VM, FANCY, FW ? FW : 1, default_slots(HM, VM, FANCY));
+            ok = run_work<HM, VM, FANCY, QM, UNI, FW>(tm, id, d, s, d.row0 + rr, d.row0 + rr + len, smem, LF, ps, err,
+                                                      last, false);
+        } else {
+            ok = run_work<HM, VM, FANCY, QM, UNI>(tm, id, d, s, d.row0 + rr, d.row0 + rr + len, smem, L, ps, err, last,
+                                                  false);
+        }
+        if (!ok) return false;
     }
     return true;
 }
