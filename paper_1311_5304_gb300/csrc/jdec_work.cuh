@@ -100,6 +100,34 @@ __device__ __forceinline__ void issue_job(const CUtensorMap *tm, const SmemLayou
     }
 }
 
+// Colour conversion of 16 pixels of one row when every pixel has its own
+// chroma sample (4:4:4, and 4:4:0 with replication): Cb bytes at cb, Cr bytes
+// `cstep` after them, luma at yrow; n1 pixels of the first 8-pixel group and
+// n2 (0: none) of the second are written to out.  Samples minus 128 are the
+// signed bytes of the words XOR 0x80808080.
+__device__ __forceinline__ void row_convert_h1(const uint8_t *cb, int cstep, const uint8_t *yrow, uint8_t *out,
+                                               int n1, int n2, bool vec)
+{
+    uint4 wb = *reinterpret_cast<const uint4 *>(cb);
+    uint4 wr = *reinterpret_cast<const uint4 *>(cb + cstep);
+    wb.x ^= 0x80808080u; wb.y ^= 0x80808080u; wb.z ^= 0x80808080u; wb.w ^= 0x80808080u;
+    wr.x ^= 0x80808080u; wr.y ^= 0x80808080u; wr.z ^= 0x80808080u; wr.w ^= 0x80808080u;
+    int Cb[2][8], Cr[2][8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        Cb[0][k] = sbyte_of(wb.x, k); Cb[0][4 + k] = sbyte_of(wb.y, k);
+        Cb[1][k] = sbyte_of(wb.z, k); Cb[1][4 + k] = sbyte_of(wb.w, k);
+        Cr[0][k] = sbyte_of(wr.x, k); Cr[0][4 + k] = sbyte_of(wr.y, k);
+        Cr[1][k] = sbyte_of(wr.z, k); Cr[1][4 + k] = sbyte_of(wr.w, k);
+    }
+    const uint2 y0 = *reinterpret_cast<const uint2 *>(yrow);
+    cc_store8(y0, Cb[0], Cr[0], out, n1, vec);
+    if (n2 > 0) {
+        const uint2 y1 = *reinterpret_cast<const uint2 *>(yrow + 8);
+        cc_store8(y1, Cb[1], Cr[1], out + 24, n2, vec);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // colour warps: one task = 16 pixels (two 8-pixel groups) of one output row
 // ---------------------------------------------------------------------------
@@ -117,19 +145,10 @@ __device__ __forceinline__ void cc_task(const ItemDesc &d, const SmemLayout &L, 
     int Cb[2][8], Cr[2][8];
     if (HM == 1) {
         // 4:4:4: chroma sample = pixel; 4:4:0 replication: chroma row y/2
-        // (samples minus 128: signed bytes of the words XOR 0x80808080)
         const uint8_t *cb = slot + (VM == 2 ? (py >> 1) : py) * L.lc + 16 * gt;
-        uint4 wb = *reinterpret_cast<const uint4 *>(cb);
-        uint4 wr = *reinterpret_cast<const uint4 *>(cb + 8 * L.lc);
-        wb.x ^= 0x80808080u; wb.y ^= 0x80808080u; wb.z ^= 0x80808080u; wb.w ^= 0x80808080u;
-        wr.x ^= 0x80808080u; wr.y ^= 0x80808080u; wr.z ^= 0x80808080u; wr.w ^= 0x80808080u;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            Cb[0][k] = sbyte_of(wb.x, k); Cb[0][4 + k] = sbyte_of(wb.y, k);
-            Cb[1][k] = sbyte_of(wb.z, k); Cb[1][4 + k] = sbyte_of(wb.w, k);
-            Cr[0][k] = sbyte_of(wr.x, k); Cr[0][4 + k] = sbyte_of(wr.y, k);
-            Cr[1][k] = sbyte_of(wr.z, k); Cr[1][4 + k] = sbyte_of(wr.w, k);
-        }
+        const bool two = 2 * gt + 1 < HM * wte && xg + 8 < d.W;
+        row_convert_h1(cb, 8 * L.lc, yrow, out, min(8, d.W - xg), two ? min(8, d.W - xg - 8) : 0, vec);
+        return;
     } else if (!FANCY) {
         // replication: chroma sample (x/2, y/VM), minus 128 as above
         const uint8_t *cb = slot + (VM == 2 ? (py >> 1) : py) * L.lc + 8 * gt;
@@ -164,6 +183,34 @@ __device__ __forceinline__ void cc_task(const ItemDesc &d, const SmemLayout &L, 
     }
 }
 
+// 4:2:0 triangular colour conversion of 8 pixels of two output rows: chroma
+// near row at pn, far rows at pu (upper output row) and pd (lower), the Cr
+// rows `cstep` bytes after the Cb rows; luma at yp and yp + ypitch; RGB to
+// out and out + pitch (the second row only when `row2`); n pixels per row.
+__device__ __forceinline__ void pair_convert_h2v2(const uint8_t *pn, const uint8_t *pu, const uint8_t *pd, int cstep,
+                                                  const uint8_t *yp, int ypitch, uint8_t *out, int64_t pitch, int n,
+                                                  bool vec, bool row2)
+{
+    const uint2 y0 = *reinterpret_cast<const uint2 *>(yp);
+    const uint2 y1 = *reinterpret_cast<const uint2 *>(yp + ypitch);
+    int Cb0[8], Cr0[8], Cb1[8], Cr1[8];
+    {
+        int n6[6], f6[6];
+        load6(pn, n6);
+        load6(pu, f6);
+        tri_h2v2(n6, f6, Cb0);
+        load6(pd, f6);
+        tri_h2v2(n6, f6, Cb1);
+        load6(pn + cstep, n6);
+        load6(pu + cstep, f6);
+        tri_h2v2(n6, f6, Cr0);
+        load6(pd + cstep, f6);
+        tri_h2v2(n6, f6, Cr1);
+    }
+    cc_store8(y0, Cb0, Cr0, out, n, vec);
+    if (row2) cc_store8(y1, Cb1, Cr1, out + pitch, n, vec);
+}
+
 // 4:2:0 triangular filtering: one task = 8 pixels of the two output rows
 // 2m and 2m+1 of MCU row r, which share the near chroma row j = 8r + m; the
 // far rows are j-1 (row 2m) and j+1 (row 2m+1), clamped to the image.  Chroma
@@ -184,25 +231,9 @@ __device__ __forceinline__ void cc_task_h2v2_pair(const ItemDesc &d, const SmemL
                       : (j > 0 ? cslots + ((job - 2) & 3) * L.slot_bytes + 7 * L.lc + 8 + 4 * g : pn);
     const uint8_t *pd = j + 1 >= d.ch ? pn
                       : (m < 7 ? pn + L.lc : cslots + (job & 3) * L.slot_bytes + 8 + 4 * g);
-    const uint2 y0 = *reinterpret_cast<const uint2 *>(yplane + 2 * m * L.ypitch + 8 * g);
-    const uint2 y1 = *reinterpret_cast<const uint2 *>(yplane + (2 * m + 1) * L.ypitch + 8 * g);
-    int Cb0[8], Cr0[8], Cb1[8], Cr1[8];
-    {
-        int n6[6], f6[6];
-        load6(pn, n6);
-        load6(pu, f6);
-        tri_h2v2(n6, f6, Cb0);
-        load6(pd, f6);
-        tri_h2v2(n6, f6, Cb1);
-        load6(pn + 8 * L.lc, n6);
-        load6(pu + 8 * L.lc, f6);
-        tri_h2v2(n6, f6, Cr0);
-        load6(pd + 8 * L.lc, f6);
-        tri_h2v2(n6, f6, Cr1);
-    }
     uint8_t *out = d.rgb + static_cast<int64_t>(y) * d.pitch + 3 * x0;
-    cc_store8(y0, Cb0, Cr0, out, n, vec);
-    if (y + 1 < d.H) cc_store8(y1, Cb1, Cr1, out + d.pitch, n, vec);
+    pair_convert_h2v2(pn, pu, pd, 8 * L.lc, yplane + 2 * m * L.ypitch + 8 * g, L.ypitch, out, d.pitch, n, vec,
+                      y + 1 < d.H);
 }
 
 // 4:4:0 triangular filtering (Alg. 1 along columns): one task = 8 pixels of
