@@ -213,9 +213,9 @@ void plan_tiles(jdec_ctx *ctx, const Geometry &g, int nrows, int force_wt, int f
         const SmemLayout L0 = smem_layout(g.hm, g.vm, g.fancy, default_wt(g), default_slots(g.hm, g.vm, g.fancy));
         const long wave = static_cast<long>(occupancy_cached(ctx, g.hm, g.vm, g.fancy, L0.total)) * ctx->sms;
         // (the padded part of the last strip, decoded but not written, stays
-        // under 2 % of the width)
+        // within 3 % of the width)
         const long pad = ((g.mcus_x + fw - 1) / fw) * static_cast<long>(fw) - g.mcus_x;
-        if (fw > 0 && g.mcus_x >= fw && 50 * pad <= g.mcus_x && enough_rows(g, nrows, wave, fw)) {
+        if (fw > 0 && g.mcus_x >= fw && 100 * pad <= 3L * g.mcus_x && enough_rows(g, nrows, wave, fw)) {
             w = fw;
             *fixed = true;
         } else {
@@ -312,7 +312,11 @@ jdec_status launch_rows(jdec_ctx *ctx, const jdec_image *img, const Geometry &g,
     bool fixed;
     const int ni = tuned_nidct(ctx, g);
     // the compile-time-width instances run the default split (64 IDCT threads)
-    const int fw = (ni > 0 && ni != 64) ? 0 : fixed_wt(g.hm, g.vm, g.fancy, qmode_of(img, g));
+    // and store whole 8-pixel groups with aligned stores only: 8-byte aligned
+    // rows, width a multiple of 8
+    const bool clean = ((reinterpret_cast<uintptr_t>(img->rgb) | static_cast<uintptr_t>(img->rgb_pitch)) & 7) == 0 &&
+                       g.W % 8 == 0;
+    const int fw = ((ni > 0 && ni != 64) || !clean) ? 0 : fixed_wt(g.hm, g.vm, g.fancy, qmode_of(img, g));
     plan_tiles(ctx, g, row1 - row0, force_wt, fw, &wt, &nctas, &smem, &fixed);
     DecodeParams p;
     memset(&p, 0, sizeof(p));

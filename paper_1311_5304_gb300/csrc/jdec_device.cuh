@@ -467,9 +467,24 @@ __device__ __forceinline__ void store24(uint8_t *out, const uint32_t w[6])
     }
 }
 
+// The rarely taken stores of an 8-pixel group, kept out of line so that the
+// hot path stays small: the 24 bytes w[0..5] (saturated R, G, B of 8 pixels)
+// to a row that is not 8-byte aligned, or the first 3n bytes only (n < 8
+// pixels inside the image, at its right edge).
+static __device__ __noinline__ void store_group_slow(uint8_t *out, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
+                                              uint32_t w4, uint32_t w5, int n)
+{
+    const uint32_t w[6] = {w0, w1, w2, w3, w4, w5};
+    if (n >= 8) {
+        store24(out, w);
+        return;
+    }
+    for (int k = 0; k < 3 * n; ++k) out[k] = static_cast<uint8_t>(w[k >> 2] >> (8 * (k & 3)));
+}
+
 // Converts 8 pixels and writes 24 bytes to `out` (global).  yw: the 8 luma
 // samples as two words; Cb, Cr: chroma minus 128; `n` = pixels inside the
-// image (1..8).
+// image (1..8); `vec`: out is 8-byte aligned.
 __device__ __forceinline__ void cc_store8(uint2 yw, const int Cb[8], const int Cr[8], uint8_t *out, int n, bool vec)
 {
     int R[8], G[8], B[8];
@@ -480,31 +495,20 @@ __device__ __forceinline__ void cc_store8(uint2 yw, const int Cb[8], const int C
         G[k] = (ys - Cb[k] * 22554 - Cr[k] * 46802) >> 16;
         B[k] = (ys + Cb[k] * 116130) >> 16;
     }
-    if (n == 8) {
-        uint32_t w[6];
-        w[0] = pack_sat4(R[0], G[0], B[0], R[1]);
-        w[1] = pack_sat4(G[1], B[1], R[2], G[2]);
-        w[2] = pack_sat4(B[2], R[3], G[3], B[3]);
-        w[3] = pack_sat4(R[4], G[4], B[4], R[5]);
-        w[4] = pack_sat4(G[5], B[5], R[6], G[6]);
-        w[5] = pack_sat4(B[6], R[7], G[7], B[7]);
-        if (vec) {
-            uint2 *o = reinterpret_cast<uint2 *>(out);
-            o[0] = make_uint2(w[0], w[1]);
-            o[1] = make_uint2(w[2], w[3]);
-            o[2] = make_uint2(w[4], w[5]);
-        } else {
-            store24(out, w);
-        }
+    uint32_t w[6];
+    w[0] = pack_sat4(R[0], G[0], B[0], R[1]);
+    w[1] = pack_sat4(G[1], B[1], R[2], G[2]);
+    w[2] = pack_sat4(B[2], R[3], G[3], B[3]);
+    w[3] = pack_sat4(R[4], G[4], B[4], R[5]);
+    w[4] = pack_sat4(G[5], B[5], R[6], G[6]);
+    w[5] = pack_sat4(B[6], R[7], G[7], B[7]);
+    if (n == 8 && vec) {
+        uint2 *o = reinterpret_cast<uint2 *>(out);
+        o[0] = make_uint2(w[0], w[1]);
+        o[1] = make_uint2(w[2], w[3]);
+        o[2] = make_uint2(w[4], w[5]);
     } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (k < n) {
-                out[3 * k + 0] = static_cast<uint8_t>(min(max(R[k], 0), 255));
-                out[3 * k + 1] = static_cast<uint8_t>(min(max(G[k], 0), 255));
-                out[3 * k + 2] = static_cast<uint8_t>(min(max(B[k], 0), 255));
-            }
-        }
+        store_group_slow(out, w[0], w[1], w[2], w[3], w[4], w[5], n);
     }
 }
 

@@ -131,14 +131,17 @@ __device__ __forceinline__ void row_convert_h1(const uint8_t *cb, int cstep, con
 // ---------------------------------------------------------------------------
 // colour warps: one task = 16 pixels (two 8-pixel groups) of one output row
 // ---------------------------------------------------------------------------
-template <int HM, int VM, bool FANCY>
+// CLEAN: the image's rows are 8-byte aligned and its width a multiple of 8,
+// so every 8-pixel group inside the image is whole and stored with aligned
+// 8-byte stores (no partial or unaligned path in the code).
+template <int HM, int VM, bool FANCY, bool CLEAN = false>
 __device__ __forceinline__ void cc_task(const ItemDesc &d, const SmemLayout &L, const uint8_t *yplane,
                                         const uint8_t *cslots, int job, int r, int mx0, int wte, int py, int gt)
 {
     const int xg = (mx0 * HM + 2 * gt) * 8;
     const int y = r * 8 * VM + py;
     if (xg >= d.W || y >= d.H) return;
-    const bool vec = d.aligned8;
+    const bool vec = CLEAN || d.aligned8;
     const uint8_t *yrow = yplane + py * L.ypitch + 16 * gt;
     uint8_t *out = d.rgb + static_cast<int64_t>(y) * d.pitch + 3 * xg;
     const uint8_t *slot = cslots + (job & (L.nslot - 1)) * L.slot_bytes;
@@ -147,7 +150,8 @@ __device__ __forceinline__ void cc_task(const ItemDesc &d, const SmemLayout &L, 
         // 4:4:4: chroma sample = pixel; 4:4:0 replication: chroma row y/2
         const uint8_t *cb = slot + (VM == 2 ? (py >> 1) : py) * L.lc + 16 * gt;
         const bool two = 2 * gt + 1 < HM * wte && xg + 8 < d.W;
-        row_convert_h1(cb, 8 * L.lc, yrow, out, min(8, d.W - xg), two ? min(8, d.W - xg - 8) : 0, vec);
+        row_convert_h1(cb, 8 * L.lc, yrow, out, CLEAN ? 8 : min(8, d.W - xg), two ? (CLEAN ? 8 : min(8, d.W - xg - 8)) : 0,
+                       vec);
         return;
     } else if (!FANCY) {
         // replication: chroma sample (x/2, y/VM), minus 128 as above
@@ -175,11 +179,11 @@ __device__ __forceinline__ void cc_task(const ItemDesc &d, const SmemLayout &L, 
         tri_h2v1(c10 + 4, Cr[1]);
     }
     const uint2 y0 = *reinterpret_cast<const uint2 *>(yrow);
-    cc_store8(y0, Cb[0], Cr[0], out, min(8, d.W - xg), vec);
+    cc_store8(y0, Cb[0], Cr[0], out, CLEAN ? 8 : min(8, d.W - xg), vec);
     // the second group may lie past the strip (odd group count) or the image
     if (2 * gt + 1 < HM * wte && xg + 8 < d.W) {
         const uint2 y1 = *reinterpret_cast<const uint2 *>(yrow + 8);
-        cc_store8(y1, Cb[1], Cr[1], out + 24, min(8, d.W - xg - 8), vec);
+        cc_store8(y1, Cb[1], Cr[1], out + 24, CLEAN ? 8 : min(8, d.W - xg - 8), vec);
     }
 }
 
@@ -216,14 +220,15 @@ __device__ __forceinline__ void pair_convert_h2v2(const uint8_t *pn, const uint8
 // far rows are j-1 (row 2m) and j+1 (row 2m+1), clamped to the image.  Chroma
 // block row r lives in slot (job - 1) & 3, the rows above and below it in
 // (job - 2) & 3 and job & 3.
+template <bool CLEAN = false>
 __device__ __forceinline__ void cc_task_h2v2_pair(const ItemDesc &d, const SmemLayout &L, const uint8_t *yplane,
                                                   const uint8_t *cslots, int job, int r, int mx0, int m, int g)
 {
     const int x0 = (2 * mx0 + g) * 8;
     const int y = 16 * r + 2 * m;
     if (x0 >= d.W || y >= d.H) return;
-    const int n = min(8, d.W - x0);
-    const bool vec = d.aligned8;
+    const int n = CLEAN ? 8 : min(8, d.W - x0);
+    const bool vec = CLEAN || d.aligned8;
     const int j = 8 * r + m;
     const uint8_t *slot = cslots + ((job - 1) & 3) * L.slot_bytes;
     const uint8_t *pn = slot + m * L.lc + 8 + 4 * g;
@@ -240,14 +245,15 @@ __device__ __forceinline__ void cc_task_h2v2_pair(const ItemDesc &d, const SmemL
 // output rows 2m and 2m+1 of MCU row r, near chroma row j = 8r + m, far rows
 // j-1 and j+1 clamped to the image; the slots rotate as in the 4:2:0 pair
 // task.  No horizontal filter: chroma column = pixel column.
+template <bool CLEAN = false>
 __device__ __forceinline__ void cc_task_h1v2_pair(const ItemDesc &d, const SmemLayout &L, const uint8_t *yplane,
                                                   const uint8_t *cslots, int job, int r, int mx0, int m, int g)
 {
     const int x0 = (mx0 + g) * 8;
     const int y = 16 * r + 2 * m;
     if (x0 >= d.W || y >= d.H) return;
-    const int n = min(8, d.W - x0);
-    const bool vec = d.aligned8;
+    const int n = CLEAN ? 8 : min(8, d.W - x0);
+    const bool vec = CLEAN || d.aligned8;
     const int j = 8 * r + m;
     const uint8_t *slot = cslots + ((job - 1) & 3) * L.slot_bytes;
     const uint8_t *pn = slot + m * L.lc + 8 * g;
@@ -424,7 +430,8 @@ struct FixedIdct {
 // FW > 0: the strip is decoded as exactly FW MCUs wide (d.wt == FW; a last
 // strip that reaches past the image's right edge is padded, see run_share), L
 // is the layout for width FW, the IDCT threads number 64: task lists and
-// offsets are compile-time (FixedIdct).  FW = 0: any strip.
+// offsets are compile-time (FixedIdct); the image is CLEAN (see cc_task:
+// aligned rows, width a multiple of 8).  FW = 0: any strip, any image.
 template <int HM, int VM, bool FANCY, int QM, int FW = 0>
 __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const ImageDesc &qsrc, int strip, int r0,
                                int r1, uint8_t *smem, const SmemLayout &L, PipeState &ps, int *err, bool last,
@@ -544,11 +551,11 @@ __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const Im
                 int py = py0, g = g0;
                 while (py < rows) {
                     if (V::kRing && HM == 2)
-                        cc_task_h2v2_pair(d, L, yplane, cslots, j, r, mx0, py, g);
+                        cc_task_h2v2_pair<FW != 0>(d, L, yplane, cslots, j, r, mx0, py, g);
                     else if (V::kRing)
-                        cc_task_h1v2_pair(d, L, yplane, cslots, j, r, mx0, py, g);
+                        cc_task_h1v2_pair<FW != 0>(d, L, yplane, cslots, j, r, mx0, py, g);
                     else
-                        cc_task<HM, VM, FANCY>(d, L, yplane, cslots, j, r, mx0, wte, py, g);
+                        cc_task<HM, VM, FANCY, FW != 0>(d, L, yplane, cslots, j, r, mx0, wte, py, g);
                     py += dpy;
                     g += dg;
                     if (g >= ngroups) { g -= ngroups; ++py; }
@@ -669,11 +676,11 @@ __device__ bool run_work_unified(const CUtensorMap *tm, const ItemDesc d, const 
             int py = py0, g = g0;
             while (py < rows) {
                 if (V::kRing && HM == 2)
-                    cc_task_h2v2_pair(d, L, yplane, cslots, j, r, mx0, py, g);
+                    cc_task_h2v2_pair<FW != 0>(d, L, yplane, cslots, j, r, mx0, py, g);
                 else if (V::kRing)
-                    cc_task_h1v2_pair(d, L, yplane, cslots, j, r, mx0, py, g);
+                    cc_task_h1v2_pair<FW != 0>(d, L, yplane, cslots, j, r, mx0, py, g);
                 else
-                    cc_task<HM, VM, FANCY>(d, L, yplane, cslots, j, r, mx0, wte, py, g);
+                    cc_task<HM, VM, FANCY, FW != 0>(d, L, yplane, cslots, j, r, mx0, wte, py, g);
                 py += dpy;
                 g += dg;
                 if (g >= ngroups) { g -= ngroups; ++py; }

@@ -187,3 +187,31 @@ def test_repeat_launches_are_deterministic(ctx, orc):
         b, _, _ = gpu_rgb(ctx, img, planes=planes)
         assert np.array_equal(a, b)
     assert_same(a, oracle_rgb(orc, img), "repeat")
+
+
+@pytest.mark.parametrize("sampling,w,h", [("420", 1912, 9725), ("420", 8184, 4097), ("444", 1272, 2001),
+                                          ("444", 8184, 1031)])
+def test_fixed_width_path_edges(ctx, orc, sampling, w, h):
+    # Large images with 8-byte aligned rows and a width that is a multiple of
+    # 8 take the compile-time-width code (4:4:4 strips of 32 MCUs, 4:2:0 of
+    # 20): a right-edge MCU half outside the image, a padded last strip
+    # (8184 = 511.5 MCUs wide), ragged heights; a forced width (general code)
+    # must give the same bytes, both equal to the oracle
+    img = synth.make_image(w, h, sampling, 88, seed=w * 7 + h, kind="texture", sigma=3.0, fancy=True)
+    planes = upload(img)
+    got, host, _ = gpu_rgb(ctx, img, planes=planes, pitch=3 * w + 8)
+    assert_padding_untouched(host, img, 3 * w + 8, 0)
+    want = oracle_rgb(orc, img)
+    assert_same(got, want, f"fixed width {sampling} {w}x{h}")
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    v = 0 if sampling == "444" else 4
+    forced = os.path.join(os.environ.get("TMPDIR", "/tmp"), f"jdec_force_{os.getpid()}.json")
+    with open(forced, "w") as f:
+        json.dump({"gpu": "x", "sms": sms, "entries": [[v, sc, 12] for sc in range(20)]}, f)
+    try:
+        with jdec.Context(tune_file=forced) as c2:
+            got2, _, _ = gpu_rgb(c2, img, planes=planes)
+    finally:
+        os.unlink(forced)
+    assert np.array_equal(got2, got)
