@@ -512,18 +512,6 @@ __device__ __forceinline__ void cc_store8(uint2 yw, const int Cb[8], const int C
     }
 }
 
-// Six samples p[-1 .. 4] around four chroma centres starting at the 4-byte
-// aligned address p.
-__device__ __forceinline__ void load6(const uint8_t *p, int c[6])
-{
-    const uint32_t l = *reinterpret_cast<const uint32_t *>(p - 4);
-    const uint32_t m = *reinterpret_cast<const uint32_t *>(p);
-    const uint32_t r = *reinterpret_cast<const uint32_t *>(p + 4);
-    c[0] = byte_of(l, 3);
-    c[1] = byte_of(m, 0); c[2] = byte_of(m, 1); c[3] = byte_of(m, 2); c[4] = byte_of(m, 3);
-    c[5] = byte_of(r, 0);
-}
-
 // Ten samples p[-1 .. 8] around eight chroma centres starting at the 4-byte
 // aligned address p.
 __device__ __forceinline__ void load10(const uint8_t *p, int c[10])
@@ -552,20 +540,39 @@ __device__ __forceinline__ void tri_h2v1(const int c[6], int o[8])
     }
 }
 
-// h2v2 triangular: vertical 3:1 sums of the near and far rows, then the
-// horizontal 3:1 filter with one rounding (+8 / +7, >> 4); outputs minus 128
-// ((x - 2048) >> 4 = (x >> 4) - 128).
-__device__ __forceinline__ void tri_h2v2(const int n[6], const int f[6], int o[8])
+// h2v2 triangular on 16-bit lane pairs (two samples per 32-bit operation; no
+// lane carries out: 3 * 1020 + 1020 + 2056 < 2^16).  The 6 samples c[-1..4]
+// of a row around four chroma centres are the bytes l.3, m.0-3, r.0 of three
+// words; lanes4 forms the pairs (c0,c2), (c1,c3), (c-1,c1), (c2,c4).
+__device__ __forceinline__ void lanes4(uint32_t l, uint32_t m, uint32_t r, uint32_t &e, uint32_t &o, uint32_t &lp,
+                                       uint32_t &rp)
 {
-    int s[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) s[k] = 3 * n[k] + f[k];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int t = 3 * s[k + 1];
-        o[2 * k] = (t + s[k] + 8 - 2048) >> 4;
-        o[2 * k + 1] = (t + s[k + 2] + 7 - 2048) >> 4;
-    }
+    e = __byte_perm(m, 0u, 0x4240);
+    o = __byte_perm(m, 0u, 0x4341);
+    lp = __byte_perm(o, l, 0x1017);
+    rp = __byte_perm(e, r, 0x1412);
+}
+
+// The 8 outputs (minus 128) of one output row from the near row's pairs
+// (ne, no, nl, nr) and the far row's words: S = 3 near + far per lane, then
+// out[2k] = (3 S_k + S_{k-1} + 8) >> 4 and out[2k+1] = (3 S_k + S_{k+1} + 7) >> 4
+// with 2048 more in each sum, so that the low byte of each lane's result is
+// the sample XOR 0x80 (read back as a signed byte: the sample minus 128).
+__device__ __forceinline__ void tri_h2v2_pairs(uint32_t ne, uint32_t no, uint32_t nl, uint32_t nr, uint32_t fl,
+                                               uint32_t fm, uint32_t fr, int out[8])
+{
+    uint32_t fe, fo, flp, frp;
+    lanes4(fl, fm, fr, fe, fo, flp, frp);
+    const uint32_t se = ne * 3u + fe, so = no * 3u + fo, sl = nl * 3u + flp, sr = nr * 3u + frp;
+    const uint32_t te = se * 3u, to = so * 3u;
+    const uint32_t p04 = (te + sl + 0x08080808u) >> 4;   // outputs 0, 4
+    const uint32_t p26 = (to + se + 0x08080808u) >> 4;   // 2, 6
+    const uint32_t p15 = (te + so + 0x08070807u) >> 4;   // 1, 5
+    const uint32_t p37 = (to + sr + 0x08070807u) >> 4;   // 3, 7
+    out[0] = sbyte_of(p04, 0); out[4] = sbyte_of(p04, 2);
+    out[2] = sbyte_of(p26, 0); out[6] = sbyte_of(p26, 2);
+    out[1] = sbyte_of(p15, 0); out[5] = sbyte_of(p15, 2);
+    out[3] = sbyte_of(p37, 0); out[7] = sbyte_of(p37, 2);
 }
 
 }  // namespace jdec

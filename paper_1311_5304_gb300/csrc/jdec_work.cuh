@@ -198,18 +198,16 @@ __device__ __forceinline__ void pair_convert_h2v2(const uint8_t *pn, const uint8
     const uint2 y0 = *reinterpret_cast<const uint2 *>(yp);
     const uint2 y1 = *reinterpret_cast<const uint2 *>(yp + ypitch);
     int Cb0[8], Cr0[8], Cb1[8], Cr1[8];
-    {
-        int n6[6], f6[6];
-        load6(pn, n6);
-        load6(pu, f6);
-        tri_h2v2(n6, f6, Cb0);
-        load6(pd, f6);
-        tri_h2v2(n6, f6, Cb1);
-        load6(pn + cstep, n6);
-        load6(pu + cstep, f6);
-        tri_h2v2(n6, f6, Cr0);
-        load6(pd + cstep, f6);
-        tri_h2v2(n6, f6, Cr1);
+#pragma unroll
+    for (int comp = 0; comp < 2; ++comp) {
+        const int o = comp * cstep;
+        const uint32_t *wn = reinterpret_cast<const uint32_t *>(pn + o);
+        const uint32_t *wu = reinterpret_cast<const uint32_t *>(pu + o);
+        const uint32_t *wd = reinterpret_cast<const uint32_t *>(pd + o);
+        uint32_t ne, no, nl, nr;
+        lanes4(wn[-1], wn[0], wn[1], ne, no, nl, nr);
+        tri_h2v2_pairs(ne, no, nl, nr, wu[-1], wu[0], wu[1], comp ? Cr0 : Cb0);
+        tri_h2v2_pairs(ne, no, nl, nr, wd[-1], wd[0], wd[1], comp ? Cr1 : Cb1);
     }
     cc_store8(y0, Cb0, Cr0, out, n, vec);
     if (row2) cc_store8(y1, Cb1, Cr1, out + pitch, n, vec);
