@@ -311,18 +311,19 @@ jdec_status launch_rows(jdec_ctx *ctx, const jdec_image *img, const Geometry &g,
     int wt, nctas, smem;
     bool fixed;
     const int ni = tuned_nidct(ctx, g);
-    // the compile-time-width instances run the default split (64 IDCT threads)
-    // and store whole 8-pixel groups with aligned stores only: 8-byte aligned
-    // rows, width a multiple of 8
+    // the compile-time-width instances run their own split (kFixedIdctThreads
+    // IDCT threads) and store whole 8-pixel groups with aligned stores only:
+    // 8-byte aligned rows, width a multiple of 8
     const bool clean = ((reinterpret_cast<uintptr_t>(img->rgb) | static_cast<uintptr_t>(img->rgb_pitch)) & 7) == 0 &&
                        g.W % 8 == 0;
-    const int fw = ((ni > 0 && ni != 64) || !clean) ? 0 : fixed_wt(g.hm, g.vm, g.fancy, qmode_of(img, g));
+    const int fw = ((ni > 0 && ni != kFixedIdctThreads) || !clean) ? 0 : fixed_wt(g.hm, g.vm, g.fancy, qmode_of(img, g));
     plan_tiles(ctx, g, row1 - row0, force_wt, fw, &wt, &nctas, &smem, &fixed);
     DecodeParams p;
     memset(&p, 0, sizeof(p));
     if (!encode_maps(p.tmap, img, g, wt)) return JDEC_ECUDA;
     fill_desc(&p.img, img, g, wt, nctas);
     if (ni > 0) p.img.nidct = ni;
+    if (fixed) p.img.nidct = kFixedIdctThreads;
     p.img.row0 = row0;
     p.img.row1 = row1;
     p.err = ctx->d_err;

@@ -119,6 +119,11 @@ struct SmemLayout {
 
 __host__ __device__ inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
+// IDCT threads of the split roles in the compile-time-width path (4:4:4,
+// 32-MCU strips: 96 blocks per job, one per IDCT thread; the fourth warp
+// converts the job's 128 16-pixel tasks, about as much work).
+constexpr int kFixedIdctThreads = 96;
+
 // Strip widths with a compile-time-width fast path in the single-image kernel
 // (the variants' default widths, 8-bit tables): 4:4:4 32 MCUs, triangular
 // 4:2:2 31, triangular 4:2:0 20; 0 = none.

@@ -8,7 +8,7 @@ namespace jdec {
 
 // unified: every warp transforms and converts (triangular 4:2:2 / 4:2:0 only);
 // fixed: the compile-time-width instance for p.img.wt == fixed_wt(...)
-// (unified roles for 4:2:2 / 4:2:0, split for 4:4:4; 64 IDCT threads)
+// (unified roles for 4:2:2 / 4:2:0, split for 4:4:4 with kFixedIdctThreads IDCT threads)
 cudaError_t launch_fused(int hm, int vm, bool fancy, bool unified, bool fixed, const DecodeParams &p, int grid,
                          int smem, cudaStream_t s);
 int fused_occupancy(int hm, int vm, bool fancy, int smem);

@@ -427,8 +427,8 @@ struct FixedIdct {
 
 // FW > 0: the strip is decoded as exactly FW MCUs wide (d.wt == FW; a last
 // strip that reaches past the image's right edge is padded, see run_share), L
-// is the layout for width FW, the IDCT threads number 64: task lists and
-// offsets are compile-time (FixedIdct); the image is CLEAN (see cc_task:
+// is the layout for width FW, kFixedIdctThreads threads transform: task lists
+// and offsets are compile-time (FixedIdct); the image is CLEAN (see cc_task:
 // aligned rows, width a multiple of 8).  FW = 0: any strip, any image.
 template <int HM, int VM, bool FANCY, int QM, int FW = 0>
 __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const ImageDesc &qsrc, int strip, int r0,
@@ -450,7 +450,7 @@ __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const Im
     const uint32_t bar0 = smem_u32(smem + L.off_bar);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L.off_flag);
 
-    const int nidct = FW ? 64 : d.nidct, ncc = kCtaThreads - nidct;
+    const int nidct = FW ? kFixedIdctThreads : d.nidct, ncc = kCtaThreads - nidct;
     if (tid < nidct) {
         // =================== IDCT warps ===================
         int *qs = reinterpret_cast<int *>(smem + L.off_q);
@@ -467,7 +467,7 @@ __device__ bool run_work_split(const CUtensorMap *tm, const ItemDesc d, const Im
         const int used = 8 * (wte + (V::kHalo ? 2 : 0));
         const bool edge = V::kHalo && (mx0 == 0 || d.cw + 7 - 8 * mx0 < used - 1);
         const uint64_t budget = 2000000000ull;   // 2 s per wait
-        FixedIdct<HM, VM, FANCY, QM, FW ? FW : 1, 64> fx;
+        FixedIdct<HM, VM, FANCY, QM, FW ? FW : 1, kFixedIdctThreads> fx;
         if (FW) fx.init(L, tid);
 
         if (tid == 0) {
