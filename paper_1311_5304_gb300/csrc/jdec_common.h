@@ -45,6 +45,9 @@ struct ImageDesc {
     int32_t nslot;          // chroma slots of the shared-memory ring (2 or 4)
     int32_t nidct;          // IDCT threads of the split roles (32, 64 or 96; unified roles: unused)
     int32_t withhold;       // testing aid: arm the load barriers, issue no loads
+    int32_t dyn_start;      // single-image launch: strip-rows before this index are split
+                            // evenly over the CTAs, the rest claimed in chunks
+    int32_t dyn_chunk;      // strip-rows per claimed chunk
     int32_t q[3][64];       // dequantisation tables, natural order (kAAN: prescaled)
 };
 
@@ -85,7 +88,14 @@ struct DecodeParams {
     CUtensorMap tmap[3];    // coefficient planes, 3-D {64, blocks_w, blocks_h}
     ImageDesc img;
     int *err;               // device error word
+    int *work;              // this launch's two counters: chunks claimed, CTAs finished
+                            // (both zero at launch; the last CTA to finish resets them)
 };
+
+// Work counters of the single-image launches: a context owns kWorkSlots pairs
+// and hands them out in turn, so up to kWorkSlots - 1 of its launches may
+// overlap on the GPU.
+constexpr int kWorkSlots = 64;
 
 // Threads of a CTA: IDCT warps (producers) + upsample/colour warps (consumers).
 constexpr int kWarps = 4;

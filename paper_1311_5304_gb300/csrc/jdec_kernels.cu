@@ -27,7 +27,8 @@ __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_fused_kernel(
     }
     __syncthreads();
     PipeState ps{0u, 0, 0};
-    run_share<HM, VM, FANCY, QM, UNI, FW>(p.tmap, p.img, blockIdx.x, smem, L, ps, p.err, true);
+    run_share<HM, VM, FANCY, QM, UNI, FW>(p.tmap, p.img, blockIdx.x, smem, L, ps, p.err, p.work);
+    finish_work(p.work);
 }
 
 template <int HM, int VM, bool FANCY, int QM, bool UNI = false, int FW = 0>

@@ -45,7 +45,9 @@ struct jdec_ctx {
     jdec_options opt;
     int device = 0;
     int sms = 0;
-    int *d_err = nullptr;
+    int *d_err = nullptr;         // error word, then kWorkSlots pairs of work counters
+    int *d_work = nullptr;
+    int work_slot = 0;
     size_t owned_bytes = 0;
     long launches = 0;
     int fail_allocs = 0;   // testing aid: the next n buffer allocations fail (JDEC_TEST_FAIL_ALLOCS)

@@ -708,28 +708,25 @@ __device__ __forceinline__ bool run_work(const CUtensorMap *tm, const ItemDesc d
 
 namespace jdec {
 
-// Runs this CTA's share of an image: the strips' MCU rows in [row0, row1),
-// concatenated strip after strip, split evenly over `nctas` CTAs; `b` is the
-// CTA's index among them.  FW > 0 (the launch's strip width, d.wt == FW):
-// every strip runs the compile-time-width code; a last strip that reaches
-// past the image's right edge is decoded as a full one (its blocks beyond the
-// edge are zero-filled by TMA, the chroma halo is replaced by the true edge,
-// and no pixel beyond the image is written).
-template <int HM, int VM, bool FANCY, int QM, bool UNI, int FW = 0>
-__device__ bool run_share(const CUtensorMap *tm, const ImageDesc &d, int b, uint8_t *smem, const SmemLayout &L,
-                          PipeState &ps, int *err, bool last_image)
+// Runs the strip-rows [a, e) of an image (strip-rows concatenated strip after
+// strip) as one item per strip.  `last_range`: the CTA decodes nothing after
+// them.  FW > 0 (the launch's strip width, d.wt == FW): every strip runs the
+// compile-time-width code; a last strip that reaches past the image's right
+// edge is decoded as a full one (its blocks beyond the edge are zero-filled by
+// TMA, the chroma halo is replaced by the true edge, and no pixel beyond the
+// image is written).
+template <int HM, int VM, bool FANCY, int QM, bool UNI, int FW>
+__device__ __forceinline__ bool run_range(const CUtensorMap *tm, const ItemDesc &id, const ImageDesc &d, long a,
+                                          long e, uint8_t *smem, const SmemLayout &L, PipeState &ps, int *err,
+                                          bool last_range)
 {
-    const ItemDesc id = item_desc(d);
     const long nrows = d.row1 - d.row0;
-    const long total = nrows * d.nstrips;
-    long a = total * b / d.nctas;
-    const long e = total * (b + 1) / d.nctas;
     while (a < e) {
         const int s = static_cast<int>(a / nrows);
         const int rr = static_cast<int>(a - s * nrows);
         const int len = static_cast<int>(min(e - a, nrows - rr));
         a += len;
-        const bool last = last_image && a >= e;
+        const bool last = last_range && a >= e;
         bool ok;
         if (FW) {
             const SmemLayout LF = smem_layout(HM, VM, FANCY, FW ? FW : 1, default_slots(HM, VM, FANCY));
@@ -742,6 +739,57 @@ __device__ bool run_share(const CUtensorMap *tm, const ImageDesc &d, int b, uint
         if (!ok) return false;
     }
     return true;
+}
+
+// Runs this CTA's share of an image (MCU rows [row0, row1) of every strip):
+// CTA b of nctas first takes its even part of the strip-rows before
+// d.dyn_start, then claims chunks of d.dyn_chunk strip-rows of the rest from
+// the launch's counter (work[0]) until none is left, so that CTAs that
+// progress faster take more.  Split roles then consume the colour warps'
+// last two EMPTY signals (the drain a final item does).
+template <int HM, int VM, bool FANCY, int QM, bool UNI, int FW = 0>
+__device__ bool run_share(const CUtensorMap *tm, const ImageDesc &d, int b, uint8_t *smem, const SmemLayout &L,
+                          PipeState &ps, int *err, int *work)
+{
+    const ItemDesc id = item_desc(d);
+    const long total = static_cast<long>(d.row1 - d.row0) * d.nstrips;
+    const long S = work ? min(static_cast<long>(d.dyn_start), total) : total;
+    if (!run_range<HM, VM, FANCY, QM, UNI, FW>(tm, id, d, S * b / d.nctas, S * (b + 1) / d.nctas, smem, L, ps, err,
+                                               S >= total))
+        return false;
+    if (S >= total) return true;
+    volatile int *claim = reinterpret_cast<volatile int *>(smem + L.off_flag + 4);
+    for (;;) {
+        __syncthreads();   // every thread has read the previous claim
+        if (threadIdx.x == 0) *claim = atomicAdd(work, 1);
+        __syncthreads();
+        const long a = S + static_cast<long>(*claim) * d.dyn_chunk;
+        if (a >= total) break;
+        if (!run_range<HM, VM, FANCY, QM, UNI, FW>(tm, id, d, a, min(a + d.dyn_chunk, total), smem, L, ps, err,
+                                                   false))
+            return false;
+    }
+    if (!(UNI && Variant<HM, VM, FANCY>::kCanUnify)) {
+        const int nidct = FW ? kFixedIdctThreads : d.nidct;
+        if (static_cast<int>(threadIdx.x) < nidct)
+            for (int jj = ps.job; jj < ps.job + 2; ++jj)
+                if (jj >= ps.sync_from + 2) named_sync(kBarEmpty0 + (jj & 1), kCtaThreads);
+        ps.sync_from = ps.job;
+    }
+    return true;
+}
+
+// The end of a single-image launch's CTA: counts it finished; the last one
+// resets the launch's counters for the next launch that uses them.
+__device__ __forceinline__ void finish_work(int *work)
+{
+    if (work && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(work + 1, 1) == static_cast<int>(gridDim.x) - 1) {
+            work[0] = 0;
+            work[1] = 0;
+        }
+    }
 }
 
 }  // namespace jdec
