@@ -7,7 +7,7 @@
  *   base_c  = smooth per-channel colour field: offset + linear ramps + a
  *             product of sinusoids;
  *   texture = 4 octaves of 2-D gradient noise (cells 24, 10, 4, 2.2 px) plus an
- *             independent 3-octave texture (16, 6, 3 px) in the colour
+ *             independent 4-octave texture (16, 6, 3, 2.2 px) in the colour
  *             difference direction, scaled by a
  *             patch mask m = clamp(4 (P(x, y) - t), 0, 1) where P is gradient
  *             noise with 192-px cells and t is set from the requested cover;
@@ -106,7 +106,8 @@ static void content_rgb(const content_t *c, int x, int y, double rgb[3])
                      + 0.5 * grad_noise(c->seed, 3, x / 4.0, y / 4.0) + 0.45 * grad_noise(c->seed, 8, x / 2.2, y / 2.2);
             /* an independent texture drives the colour difference channels */
             double t2 = grad_noise(c->seed, 5, x / 16.0, y / 16.0) + 0.7 * grad_noise(c->seed, 6, x / 6.0, y / 6.0)
-                      + 0.6 * grad_noise(c->seed, 9, x / 3.0, y / 3.0);
+                      + 0.6 * grad_noise(c->seed, 9, x / 3.0, y / 3.0)
+                      + 0.9 * grad_noise(c->seed, 10, x / 2.2, y / 2.2);
             double amp = 70.0 * m;
             rgb[0] += amp * (t + 1.0 * t2);
             rgb[1] += amp * (t - 0.5 * t2);
