@@ -34,3 +34,17 @@ def test_quality_scaling_follows_the_ijg_rule():
         s = 5000 // q if q < 50 else 200 - 2 * q
         want = np.clip((base * s + 50) // 100, 1, 255)
         assert np.array_equal(synth.make_image(16, 16, "444", q, seed=1).qtabs[0], want), q
+
+
+@pytest.mark.parametrize("sampling", ["444", "422", "420"])
+def test_large_image_content_has_its_nonzero_ac_band(sampling):
+    # The 8192x8192 q90 texture images (cover 0.85, grain 4) have 30-60 % of
+    # their AC coefficients nonzero over all planes, chroma included, with the
+    # fraction falling along zig-zag order.  The statistics are local (texture
+    # cells of at most 192 px), so a 1024x1024 crop of the same recipe shows them.
+    img = synth.make_image(1024, 1024, sampling, 90, seed=13115304 + 2000, kind="texture", sigma=4.0, cover=0.85)
+    assert 0.30 <= synth.nonzero_ac_fraction(img) <= 0.60
+    for p in img.planes[1:]:
+        assert np.count_nonzero(p[..., 1:]) / p[..., 1:].size >= 0.25
+    nz = sum(np.count_nonzero(p, axis=(0, 1)) for p in img.planes)
+    assert nz[1] > nz[20] > nz[63]
