@@ -2,10 +2,11 @@
 //
 // Host side of jdec_decode_batch: every image is cut into strips of its
 // variant's width; for each variant class (sampling, upsampling, and the
-// dequantisation/IDCT mode: LLM with 8-bit or 16-bit tables, or AAN) the strips' MCU rows of its images, concatenated image after
-// image, are weighted by their decode cost and split into equal contiguous
-// shares, one per resident CTA of that class's kernel.  Each class runs as one
-// persistent launch over its (image, strip, row range) work list, holding
+// dequantisation/IDCT mode: LLM with 8-bit or 16-bit tables, or AAN) the
+// strips' MCU rows of its images are cut into runs of at most a third of an
+// even share of the class's decode cost per resident CTA, costliest first.
+// Each class runs as one persistent launch whose CTAs claim the (image, strip,
+// row range) runs from a counter as they finish the previous one, holding
 // only that variant's code; the launches follow each other on the stream.
 // The per-image descriptors (TMA tensor maps, geometry, quantisation tables)
 // and the work lists are written to pinned staging memory and copied to a
@@ -48,15 +49,15 @@ struct MapKeyHash {
     }
 };
 
-// One class launch of a batch: grid, shared memory, layout, and where its
-// per-CTA item offsets start in the staging buffer.
+// One class launch of a batch: grid, shared memory, layout, and its items
+// (item0 .. item0 + nitems - 1 of the work list, claimed by the CTAs).
 struct ClassLaunch {
     int cls, nctas, smem;
-    size_t first_off;
+    int32_t item0, nitems;
     UnionLayout U;
     bool operator==(const ClassLaunch &o) const
     {
-        return cls == o.cls && nctas == o.nctas && smem == o.smem && first_off == o.first_off &&
+        return cls == o.cls && nctas == o.nctas && smem == o.smem && item0 == o.item0 && nitems == o.nitems &&
                memcmp(&U, &o.U, sizeof(U)) == 0;
     }
 };
@@ -72,14 +73,14 @@ struct GraphEntry {
 }  // namespace
 
 // A batch's plan: per image its strip width and class; per class present the
-// union shared-memory layout, the IDCT threads of its split roles and the
-// cost-balanced split of its strip-rows over one wave of that class's CTAs.
+// union shared-memory layout, the IDCT threads of its split roles, one wave of
+// that class's CTAs and its work list (strip-row runs of at most a third of a
+// CTA's even share of the cost, the costliest first).
 struct Plan {
     std::vector<int> wt, var, cls_of;
     int nidct[kClasses];
     std::vector<ClassLaunch> launches;
     std::vector<BatchItem> items;
-    std::vector<int32_t> first;
 };
 
 struct BatchState {
@@ -91,6 +92,7 @@ struct BatchState {
     bool copy_pending[2] = {false, false};
     int slot = 0;                                 // staging buffer of the next call
     cudaStream_t cap_stream = nullptr;
+    int *d_work = nullptr;                        // two counters per class launch (see BatchParams)
     std::vector<GraphEntry> graphs;
     std::unordered_map<MapKey, CUtensorMap, MapKeyHash> maps;
     Plan plan;                                    // the latest call's plan (vectors reused)
@@ -237,7 +239,8 @@ static jdec_status build_plan(jdec_ctx *ctx, const jdec_image *imgs, const Geome
     }
     P.launches.clear();
     P.items.clear();
-    P.first.clear();
+    struct Cut { BatchItem it; double cost; };
+    std::vector<Cut> cuts;
     for (int cls = 0; cls < kClasses; ++cls) {
         if (segs[cls].empty()) continue;
         const int smem = U[cls].total;
@@ -245,47 +248,40 @@ static jdec_status build_plan(jdec_ctx *ctx, const jdec_image *imgs, const Geome
         if (occ <= 0) return JDEC_ECUDA;
         const int nctas = static_cast<int>(std::max<long>(1, std::min<long>(static_cast<long>(occ) * ctx->sms,
                                                                             rows_of[cls])));
-        std::vector<std::vector<BatchItem>> per_cta(nctas);
-        const double share = total[cls] / nctas;
-        int cta = 0;
-        double acc = 0.0;   // cost assigned to CTAs < cta plus the current CTA's part
+        // runs of at most a third of an even share (4:2:0 and 4:4:0
+        // triangular runs of at least 6 rows where the strip has them: each
+        // run decodes two chroma rows more than it converts)
+        const double cap = total[cls] / nctas / 3.0;
+        const int min_rows = (cls / kQModes == 4 || cls / kQModes == 6) ? 6 : 1;
+        cuts.clear();
         for (const Seg &sg : segs[cls]) {
-            int r = 0;
-            while (r < sg.rows) {
-                const double room = (cta + 1) * share - acc;
-                int take = sg.rows - r;
-                if (cta < nctas - 1) {
-                    const int fit = static_cast<int>(room / sg.row_cost + 0.5);
-                    take = std::max(1, std::min(take, fit));
-                }
-                per_cta[cta].push_back(BatchItem{sg.img, sg.strip, r, r + take});
+            const int per = std::max(min_rows, static_cast<int>(cap / sg.row_cost));
+            for (int r = 0; r < sg.rows;) {
+                const int take = std::min(sg.rows - r, per);
+                cuts.push_back(Cut{BatchItem{sg.img, sg.strip, r, r + take}, take * sg.row_cost});
                 r += take;
-                acc += take * sg.row_cost;
-                if (cta < nctas - 1 && acc >= (cta + 1) * share - 0.5 * sg.row_cost) ++cta;
             }
         }
-        P.launches.push_back(ClassLaunch{cls, nctas, smem, P.first.size(), U[cls]});
-        for (int c = 0; c < nctas; ++c) {
-            P.first.push_back(static_cast<int32_t>(P.items.size()));
-            P.items.insert(P.items.end(), per_cta[c].begin(), per_cta[c].end());
-        }
-        P.first.push_back(static_cast<int32_t>(P.items.size()));
+        // the costliest runs first, so that the last ones claimed are short
+        std::stable_sort(cuts.begin(), cuts.end(), [](const Cut &a, const Cut &b) { return a.cost > b.cost; });
+        const int32_t item0 = static_cast<int32_t>(P.items.size());
+        for (const Cut &c : cuts) P.items.push_back(c.it);
+        P.launches.push_back(ClassLaunch{cls, nctas, smem, item0, static_cast<int32_t>(cuts.size()), U[cls]});
     }
     return JDEC_OK;
 }
 
-// Staging layout of a plan: images | items | cta_first (offsets bucketed so
-// that similar batches share a recorded graph).
+// Staging layout of a plan: images | items (sizes bucketed so that similar
+// batches share a recorded graph).
 struct StagingLayout {
-    size_t off_items, off_first, bytes;
+    size_t off_items, bytes;
 };
 
 static StagingLayout staging_layout(int n, const Plan &P)
 {
     const size_t img_bytes = align_up(pow2_at_least(static_cast<size_t>(n), 16) * sizeof(BatchImage), 256);
     const size_t item_bytes = align_up(pow2_at_least(P.items.size(), 256) * sizeof(BatchItem), 256);
-    const size_t first_bytes = align_up(pow2_at_least(P.first.size(), 256) * sizeof(int32_t), 256);
-    return StagingLayout{img_bytes, img_bytes + item_bytes, img_bytes + item_bytes + first_bytes};
+    return StagingLayout{img_bytes, img_bytes + item_bytes};
 }
 
 // Writes the per-image descriptors (tensor maps, geometry, tables) and the
@@ -315,7 +311,6 @@ static jdec_status write_staging(BatchState *b, const jdec_image *imgs, const Ge
         bi.variant = P.var[i];
     }
     memcpy(h + SL.off_items, P.items.data(), P.items.size() * sizeof(BatchItem));
-    memcpy(h + SL.off_first, P.first.data(), P.first.size() * sizeof(int32_t));
     return JDEC_OK;
 }
 
@@ -324,9 +319,12 @@ static BatchParams class_params(jdec_ctx *ctx, BatchState *b, const StagingLayou
     BatchParams p;
     p.imgs = static_cast<const BatchImage *>(b->d_buf);
     p.items = reinterpret_cast<const BatchItem *>(static_cast<uint8_t *>(b->d_buf) + SL.off_items);
-    p.cta_first = reinterpret_cast<const int32_t *>(static_cast<uint8_t *>(b->d_buf) + SL.off_first) + cl.first_off;
+    p.cta_first = nullptr;
     p.U = cl.U;
     p.err = ctx->d_err;
+    p.work = b->d_work + 2 * cl.cls;
+    p.item0 = cl.item0;
+    p.nitems = cl.nitems;
     return p;
 }
 
@@ -420,7 +418,10 @@ jdec_status decode_batch(jdec_ctx *ctx, const jdec_image *imgs, int n, cudaStrea
         if (!ctx->batch) return JDEC_ENOMEM;
         if (cudaEventCreateWithFlags(&ctx->batch->copied[0], cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&ctx->batch->copied[1], cudaEventDisableTiming) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&ctx->batch->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaStreamCreateWithFlags(&ctx->batch->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaMalloc(&ctx->batch->d_work, 2 * kClasses * sizeof(int)) != cudaSuccess ||
+            cudaMemset(ctx->batch->d_work, 0, 2 * kClasses * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
             release_batch(ctx);   // a later call starts over instead of using half-made state
             return JDEC_ECUDA;
         }
@@ -508,6 +509,7 @@ void release_batch(jdec_ctx *ctx)
         if (b->copied[k]) cudaEventDestroy(b->copied[k]);
     }
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->d_work) cudaFree(b->d_work);
     delete b;
     ctx->batch = nullptr;
 }

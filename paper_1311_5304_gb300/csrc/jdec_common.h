@@ -73,14 +73,19 @@ struct BatchItem {
     int32_t img, strip, r0, r1;
 };
 
-// Kernel parameters of the batched launch.  CTA b runs items
-// [cta_first[b], cta_first[b+1]) in order.
+// Kernel parameters of the batched launches.  The mixed-class launch (static
+// scratch): CTA b runs items [cta_first[b], cta_first[b+1]) in order.  A class
+// launch: the CTAs claim items item0 .. item0 + nitems - 1 one at a time from
+// the counter work[0] (work[1] counts finished CTAs; both zero at launch, the
+// last CTA to finish resets them).
 struct BatchParams {
     const BatchImage *imgs;
     const BatchItem *items;
     const int32_t *cta_first;
     UnionLayout U;
     int *err;
+    int *work;
+    int32_t item0, nitems;
 };
 
 // Kernel parameters of the single-image launch.

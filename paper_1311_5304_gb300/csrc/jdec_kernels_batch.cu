@@ -90,10 +90,14 @@ int batch_occupancy(int smem)
     return n > 0 ? n : 1;
 }
 
-//   jdec_batch_class_kernel<HM, VM, FANCY, QM>: the same work-list walk for
-//     the items of one variant class only, so each launch holds one variant's
-//     code (no instruction-cache competition between variants, registers
-//     allocated for that variant alone).
+//   jdec_batch_class_kernel<HM, VM, FANCY, QM>: the items of one variant
+//     class only, so each launch holds one variant's code (no
+//     instruction-cache competition between variants, registers allocated
+//     for that variant alone).  The CTAs claim the items one at a time from
+//     the launch's counter as they finish the previous one: CTAs on one SM
+//     progress at different rates, and items of small images cost more per
+//     pixel than their share of the pixels says, so a fixed split leaves SMs
+//     idle towards the end.  Each item drains the split-role pipeline.
 template <int HM, int VM, bool FANCY, int QM>
 __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS)
     jdec_batch_class_kernel(const __grid_constant__ BatchParams p)
@@ -107,15 +111,21 @@ __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS)
     }
     __syncthreads();
     PipeState ps{0u, 0, 0};
-    const int i0 = p.cta_first[blockIdx.x], i1 = p.cta_first[blockIdx.x + 1];
+    volatile int *claim = reinterpret_cast<volatile int *>(smem + p.U.off_flag + 4);
     int cur = -1;
-    for (int i = i0; i < i1; ++i) {
-        const BatchItem it = p.items[i];
+    for (;;) {
+        __syncthreads();   // every thread has read the previous claim
+        if (threadIdx.x == 0) *claim = atomicAdd(p.work, 1);
+        __syncthreads();
+        const int c = *claim;
+        if (c >= p.nitems) break;
+        const BatchItem it = p.items[p.item0 + c];
         const BatchImage &bi = p.imgs[it.img];
         const bool reload = it.img != cur;
         cur = it.img;
-        if (!batch_item<HM, VM, FANCY, QM>(p, bi, it, smem, ps, i + 1 == i1, reload)) break;
+        if (!batch_item<HM, VM, FANCY, QM>(p, bi, it, smem, ps, true, reload)) break;
     }
+    finish_work(p.work);
 }
 
 template <int HM, int VM, bool FANCY, int QM>

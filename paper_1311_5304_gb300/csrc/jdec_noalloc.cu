@@ -213,6 +213,9 @@ jdec_status decode_batch_static(const jdec_image *imgs, int n, cudaStream_t s)
     p.cta_first = reinterpret_cast<const int32_t *>(dscratch + kStaticFirstOff);
     p.U = U;
     p.err = reinterpret_cast<int *>(dscratch);
+    p.work = nullptr;
+    p.item0 = 0;
+    p.nitems = 0;
     if (launch_batch(p, nctas, U.total, s) != cudaSuccess) return JDEC_ECUDA;
     return JDEC_OK;
 }
