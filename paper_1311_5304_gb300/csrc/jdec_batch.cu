@@ -3,7 +3,7 @@
 // Host side of jdec_decode_batch: every image is cut into strips of its
 // variant's width; for each variant class (sampling, upsampling, and the
 // dequantisation/IDCT mode: LLM with 8-bit or 16-bit tables, or AAN) the
-// strips' MCU rows of its images are cut into runs of at most a third of an
+// strips' MCU rows of its images are cut into runs of at most a sixth of an
 // even share of the class's decode cost per resident CTA, costliest first.
 // Each class runs as one persistent launch whose CTAs claim the (image, strip,
 // row range) runs from a counter as they finish the previous one, holding
@@ -74,7 +74,7 @@ struct GraphEntry {
 
 // A batch's plan: per image its strip width and class; per class present the
 // union shared-memory layout, the IDCT threads of its split roles, one wave of
-// that class's CTAs and its work list (strip-row runs of at most a third of a
+// that class's CTAs and its work list (strip-row runs of at most a sixth of a
 // CTA's even share of the cost, the costliest first).
 struct Plan {
     std::vector<int> wt, var, cls_of;
@@ -248,10 +248,12 @@ static jdec_status build_plan(jdec_ctx *ctx, const jdec_image *imgs, const Geome
         if (occ <= 0) return JDEC_ECUDA;
         const int nctas = static_cast<int>(std::max<long>(1, std::min<long>(static_cast<long>(occ) * ctx->sms,
                                                                             rows_of[cls])));
-        // runs of at most a third of an even share (4:2:0 and 4:4:0
-        // triangular runs of at least 6 rows where the strip has them: each
-        // run decodes two chroma rows more than it converts)
-        const double cap = total[cls] / nctas / 3.0;
+        // runs of at most a sixth of an even share (measured on the 1024-image
+        // batch: a half 8.98 ms, a third 8.85, a quarter 8.67, a sixth 8.59,
+        // an eighth 8.58); 4:2:0 and 4:4:0 triangular runs of at least 6 rows
+        // where the strip has them: each run decodes two chroma rows more
+        // than it converts
+        const double cap = total[cls] / nctas / 6.0;
         const int min_rows = (cls / kQModes == 4 || cls / kQModes == 6) ? 6 : 1;
         cuts.clear();
         for (const Seg &sg : segs[cls]) {
