@@ -3,12 +3,16 @@
 // the CPU; Sec. 4.5: it overlaps with the data-parallel back-end).
 //
 // Parsing follows ITU-T T.81 markers (SOI, DQT, SOF0/SOF1, DHT, DRI, SOS).
-// Decoding uses a 64-bit bit buffer refilled a byte at a time (byte stuffing
-// 0xFF00 removed, a marker ends the data) and, per Huffman table, a 9-bit
-// lookahead table giving code length and symbol for short codes, with the
-// canonical MAXCODE/VALPTR search for longer ones.  Coefficients are written
-// in natural order into the component planes (zig-zag undone); restart
-// markers reset the DC predictors.
+// Decoding uses a 64-bit bit buffer (byte stuffing 0xFF00 removed, a marker
+// ends the data), refilled up to 8 bytes at a time when none of them is 0xFF
+// and a byte at a time otherwise.  Per Huffman table, an 11-bit table gives,
+// for a code and its magnitude bits that fit in 11 bits together, the
+// decoded value, the zero run (AC) and the bits used, so that most
+// coefficients take one lookup; other codes go through a 9-bit lookahead
+// table of code length and symbol, then the canonical MAXCODE/VALPTR search
+// for codes longer than 9 bits (T.81 F.2.2.3).  Coefficients are written in
+// natural order into the component planes (zig-zag undone); restart markers
+// reset the DC predictors.
 #include <cstdint>
 #include <cstring>
 #include <algorithm>
@@ -24,6 +28,7 @@
 namespace {
 
 constexpr int kLook = 9;
+constexpr int kFast = 11;
 
 struct HuffTable {
     bool present = false;
@@ -32,7 +37,45 @@ struct HuffTable {
     int32_t maxcode[18];     // largest code of each length (-1: none), [17] sentinel
     int32_t valoff[17];      // vals index of the first code of each length minus that code
     uint16_t look[1 << kLook];   // (length << 8) | symbol, length 0 = not in table
+    // code + magnitude bits within kFast bits: value << 16 | run << 8 | bits
+    // used; end of block: 0x80 << 8 | code length (0: not in table; never
+    // holds ZRL or sizes above 11)
+    int32_t fast[1 << kFast];
 };
+
+inline int extend(int v, int s) { return (s && v < (1 << (s - 1))) ? v - (1 << s) + 1 : v; }
+
+// Fills t.fast: for every kFast-bit prefix whose leading code (length l,
+// symbol rs: run rs >> 4, size rs & 15) and its size magnitude bits fit in
+// the prefix, the extended value, the run and l + size.  `ac`: AC table
+// (end of block flagged, ZRL left to the general path); else DC (run 0, size
+// rs).
+void build_fast(HuffTable &t, bool ac)
+{
+    memset(t.fast, 0, sizeof(t.fast));
+    int code = 0, k = 0;
+    for (int l = 1; l <= kFast; ++l) {
+        for (int i = 0; i < t.bits[l]; ++i, ++k, ++code) {
+            const int rs = t.vals[k];
+            const int run = ac ? rs >> 4 : 0, sz = ac ? rs & 15 : rs;
+            if (ac && rs == 0) {
+                // end of block: run field 0x80, no value
+                const int rest = kFast - l;
+                for (int f = 0; f < (1 << rest); ++f) t.fast[(code << rest) | f] = (0x80 << 8) | l;
+                continue;
+            }
+            if ((ac && sz == 0) || sz > (ac ? 10 : 11) || l + sz > kFast) continue;
+            const int rest = kFast - l - sz;
+            for (int m = 0; m < (1 << sz); ++m) {
+                const int v = extend(m, sz);
+                const int32_t e = static_cast<int32_t>(static_cast<uint32_t>(v) << 16) | (run << 8) | (l + sz);
+                const int base = (((code << sz) | m) << rest);
+                for (int f = 0; f < (1 << rest); ++f) t.fast[base | f] = e;
+            }
+        }
+        code <<= 1;
+    }
+}
 
 bool build_table(HuffTable &t)
 {
@@ -65,6 +108,16 @@ bool build_table(HuffTable &t)
     return true;
 }
 
+inline uint64_t load_be64(const uint8_t *p)
+{
+    uint64_t x;
+    memcpy(&x, p, 8);
+#if defined(__BYTE_ORDER__) && __BYTE_ORDER__ == __ORDER_LITTLE_ENDIAN__
+    x = __builtin_bswap64(x);
+#endif
+    return x;
+}
+
 struct BitReader {
     const uint8_t *p, *end;
     uint64_t acc = 0;   // bits are left-aligned: the next bit is bit 63
@@ -73,6 +126,20 @@ struct BitReader {
 
     void refill()
     {
+        // fast path: the next 8 bytes are data bytes with no 0xFF among them
+        if (!marker && end - p >= 8) {
+            const uint64_t x = load_be64(p);
+            const uint64_t y = ~x;   // a 0xFF byte of x is a zero byte of y
+            if (((y - 0x0101010101010101ull) & ~y & 0x8080808080808080ull) == 0) {
+                const int k = (64 - n) >> 3;   // whole bytes that fit
+                if (k > 0) {
+                    acc |= (x >> (64 - 8 * k)) << (64 - 8 * k - n);
+                    p += k;
+                    n += 8 * k;
+                }
+                return;
+            }
+        }
         while (n <= 56) {
             uint32_t byte = 0;
             if (!marker && p < end) {
@@ -132,8 +199,6 @@ inline int decode_symbol(BitReader &br, const HuffTable &t)
     br.skip(l);
     return t.vals[t.valoff[l] + code];
 }
-
-inline int extend(int v, int s) { return (s && v < (1 << (s - 1))) ? v - (1 << s) + 1 : v; }
 
 int u16be(const uint8_t *p) { return (p[0] << 8) | p[1]; }
 
@@ -204,7 +269,10 @@ jdec_status parse(const uint8_t *data, size_t size, Parsed &P, bool need_tables)
                 }
                 if (total > 256 || s + 17 + total > se) return JDEC_EINVAL;
                 memcpy(t.vals, s + 17, static_cast<size_t>(total));
-                if (need_tables && !build_table(t)) return JDEC_EINVAL;
+                if (need_tables) {
+                    if (!build_table(t)) return JDEC_EINVAL;
+                    build_fast(t, tc != 0);
+                }
                 t.present = true;
                 s += 17 + total;
             }
@@ -329,11 +397,28 @@ jdec_status decode_mcus(const Parsed &P, ScanState &S, int16_t *const planes[3],
                     const long by = static_cast<long>(mcy) * in.v_samp[c] + v;
                     int16_t *blk = planes[c] + 64 * (by * in.blocks_w[c] + bx);
                     memset(blk, 0, 64 * sizeof(int16_t));
-                    const int t = decode_symbol(br, dct);
-                    if (t < 0 || t > 11) return JDEC_EINVAL;
-                    S.pred[c] += extend(br.get(t), t);
+                    if (br.n < 32) br.refill();
+                    const int32_t fd = dct.fast[br.peek(kFast)];
+                    if (fd) {
+                        br.skip(fd & 0xff);
+                        S.pred[c] += fd >> 16;
+                    } else {
+                        const int t = decode_symbol(br, dct);
+                        if (t < 0 || t > 11) return JDEC_EINVAL;
+                        S.pred[c] += extend(br.get(t), t);
+                    }
                     blk[0] = static_cast<int16_t>(S.pred[c]);
                     for (int k = 1; k < 64; ++k) {
+                        if (br.n < 32) br.refill();
+                        const int32_t fa = act.fast[br.peek(kFast)];
+                        if (fa) {
+                            br.skip(fa & 0xff);
+                            if (fa & 0x8000) break;   // end of block
+                            k += (fa >> 8) & 0xff;
+                            if (k > 63) return JDEC_EINVAL;
+                            blk[zz[k]] = static_cast<int16_t>(fa >> 16);
+                            continue;
+                        }
                         const int rs = decode_symbol(br, act);
                         if (rs < 0) return JDEC_EINVAL;
                         const int r = rs >> 4, sz = rs & 15;
