@@ -42,6 +42,36 @@ def test_dense_coefficients_long_codes_and_stuffing():
             assert np.array_equal(planes[c], img.planes[c])
 
 
+def test_every_run_length_size_and_large_dc_steps(orc):
+    # Sparse coefficients at random positions (zero runs of every length,
+    # ZRL codes for runs of 16 or more, end of block anywhere), magnitudes of
+    # every size 1..10 and DC steps of size 11: codes and magnitude bits that
+    # fit the decoder's 11-bit combined table, ones that do not, and codes
+    # longer than its 9-bit lookahead, mixed in one stream.
+    rng = np.random.default_rng(5304)
+    img = synth.random_image(rng, 152, 104, "420")
+    for p in img.planes:
+        ac = np.zeros(p[..., 1:].shape, np.int16)
+        n = ac.shape[-1]
+        nnz = rng.integers(0, 12, size=ac.shape[:-1])
+        for idx in np.ndindex(*ac.shape[:-1]):
+            pos = rng.choice(n, size=int(nnz[idx]), replace=False)
+            size = rng.integers(1, 11, size=pos.size)
+            mag = rng.integers(1 << (size - 1), 1 << size)
+            ac[idx + (pos,)] = np.where(rng.integers(0, 2, size=pos.size) == 1, mag, -mag)
+        p[..., 1:] = ac
+        # alternate the DC between the extremes: differences of size 11
+        dc = np.where(rng.integers(0, 2, size=p[..., 0].shape) == 1, 1020, -1020)
+        p[..., 0] = dc + rng.integers(-3, 4, size=dc.shape)
+    for restart in (0, 2):
+        data = synth.encode_jfif(img, restart)
+        _, planes = _decode(data)
+        _, oplanes = orc.jpeg_decode_coefs(data)
+        for c in range(3):
+            assert np.array_equal(planes[c], img.planes[c])
+            assert np.array_equal(planes[c], oplanes[c])
+
+
 def test_rejects_malformed_and_unsupported():
     img = synth.make_image(32, 32, "420", 75)
     data = synth.encode_jfif(img)
