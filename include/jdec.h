@@ -233,8 +233,8 @@ JDEC_API jdec_status jdec_decode_jpeg(jdec_ctx *ctx, const uint8_t *data, size_t
  * 16384 items (about 64 strips of one MCU row per image at 128 images);
  * larger requests return JDEC_EINVAL and launch nothing.  Results equal
  * jdec_decode_batch.  Runs on the CURRENT device; the first call on a device
- * looks up the array's device address (cudaGetSymbolAddress), so make that
- * first call before any stream capture.  The descriptors are copied from a
+ * looks up the array's device address (cudaGetSymbolAddress) and later calls
+ * reuse it.  The descriptors are copied from a
  * static host buffer with a pageable copy, which waits for earlier work on
  * `stream` before it starts; the call returns once they are staged.  All calls
  * share the array and it keeps the last call's contents: calls whose work

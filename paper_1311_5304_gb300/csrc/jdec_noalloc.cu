@@ -13,8 +13,8 @@
 //
 // The array's name is only a host-side stand-in in host code: the first call
 // on each device (with that device current) asks the runtime for its device
-// address with cudaGetSymbolAddress and keeps it; that first call should come
-// before any stream capture.  Later calls reuse the address.
+// address with cudaGetSymbolAddress and keeps it.  Later calls reuse the
+// address.
 //
 // Every call shares the array and it keeps the previous call's contents, so
 // calls whose work overlaps on the GPU (on different streams, or a second call
