@@ -22,6 +22,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "jdec_batch_types.h"
 #include "jdec_launch.h"
 #include "jdec_runtime.h"
 
@@ -321,7 +322,6 @@ static BatchParams class_params(jdec_ctx *ctx, BatchState *b, const StagingLayou
     BatchParams p;
     p.imgs = static_cast<const BatchImage *>(b->d_buf);
     p.items = reinterpret_cast<const BatchItem *>(static_cast<uint8_t *>(b->d_buf) + SL.off_items);
-    p.cta_first = nullptr;
     p.U = cl.U;
     p.err = ctx->d_err;
     p.work = b->d_work + 2 * cl.cls;

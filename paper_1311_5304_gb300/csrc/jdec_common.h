@@ -60,34 +60,6 @@ struct UnionLayout {
     int nslot;   // chroma slots (4 when items of several variants share the layout)
 };
 
-// One image of a batched launch (device memory, 128-byte aligned: the tensor
-// maps are read from global memory by TMA).
-struct alignas(128) BatchImage {
-    CUtensorMap tmap[3];
-    ImageDesc desc;
-    int32_t variant;        // 0: 4:4:4, 1/2: 4:2:2, 3/4: 4:2:0, 5/6: 4:4:0 (replicate / triangular)
-};
-
-// A run of MCU rows [r0, r1) of one strip of one image.
-struct BatchItem {
-    int32_t img, strip, r0, r1;
-};
-
-// Kernel parameters of the batched launches.  The mixed-class launch (static
-// scratch): CTA b runs items [cta_first[b], cta_first[b+1]) in order.  A class
-// launch: the CTAs claim items item0 .. item0 + nitems - 1 one at a time from
-// the counter work[0] (work[1] counts finished CTAs; both zero at launch, the
-// last CTA to finish resets them).
-struct BatchParams {
-    const BatchImage *imgs;
-    const BatchItem *items;
-    const int32_t *cta_first;
-    UnionLayout U;
-    int *err;
-    int *work;
-    int32_t item0, nitems;
-};
-
 // Kernel parameters of the single-image launch.
 struct DecodeParams {
     CUtensorMap tmap[3];    // coefficient planes, 3-D {64, blocks_w, blocks_h}

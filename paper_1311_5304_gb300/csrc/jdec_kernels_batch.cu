@@ -1,4 +1,5 @@
 // jdec_kernels_batch.cu -- __global__ entry points of the batched launches.
+#include "jdec_batch_types.h"
 #include "jdec_kernels.cuh"
 
 namespace jdec {
@@ -22,8 +23,8 @@ __device__ __forceinline__ bool batch_item(const BatchParams &p, const BatchImag
 
 //   jdec_batch_kernel: many images of any variants in one launch (used by the
 //     allocation-free entry point, whose static scratch holds one work list);
-//     CTA b runs the items [cta_first[b], cta_first[b+1]) of a flattened
-//     (image, strip, row range) work list, pipelined across item boundaries.
+//     the CTAs claim the (image, strip, row range) items one at a time from
+//     the launch's counter, as the class launches below do.
 __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_batch_kernel(const __grid_constant__ BatchParams p)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -35,14 +36,19 @@ __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_batch_kernel(
     }
     __syncthreads();
     PipeState ps{0u, 0, 0};
-    const int i0 = p.cta_first[blockIdx.x], i1 = p.cta_first[blockIdx.x + 1];
+    volatile int *claim = reinterpret_cast<volatile int *>(smem + p.U.off_flag + 4);
     int cur = -1;
-    for (int i = i0; i < i1; ++i) {
-        const BatchItem it = p.items[i];
+    for (;;) {
+        __syncthreads();   // every thread has read the previous claim
+        if (threadIdx.x == 0) *claim = atomicAdd(p.work, 1);
+        __syncthreads();
+        const int c = *claim;
+        if (c >= p.nitems) break;
+        const BatchItem it = p.items[p.item0 + c];
         const BatchImage &bi = p.imgs[it.img];
         const bool reload = it.img != cur;
         cur = it.img;
-        const bool last = i + 1 == i1;
+        const bool last = true;   // each item drains the split-role pipeline
         bool ok;
         switch (kQModes * bi.variant + bi.desc.qmode) {
         case 0: ok = batch_item<1, 1, false, kQ16>(p, bi, it, smem, ps, last, reload); break;
@@ -70,6 +76,7 @@ __global__ void __launch_bounds__(kCtaThreads, JDEC_MIN_CTAS) jdec_batch_kernel(
         }
         if (!ok) break;
     }
+    finish_work(p.work);
 }
 
 cudaError_t launch_batch(const BatchParams &p, int grid, int smem, cudaStream_t s)

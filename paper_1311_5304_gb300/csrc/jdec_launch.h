@@ -6,6 +6,8 @@
 
 namespace jdec {
 
+struct BatchParams;   // jdec_batch_types.h
+
 // unified: every warp transforms and converts (triangular 4:2:2 / 4:2:0 only);
 // fixed: the compile-time-width instance for p.img.wt == fixed_wt(...)
 // (unified roles for 4:2:2 / 4:2:0, split for 4:4:4 with kFixedIdctThreads IDCT threads)

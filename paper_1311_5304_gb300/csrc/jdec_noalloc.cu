@@ -26,23 +26,25 @@
 #include <cstring>
 #include <mutex>
 
+#include "jdec_batch_types.h"
 #include "jdec_launch.h"
 #include "jdec_runtime.h"
 
 namespace jdec {
 
-// Capacity of the static scratch: 512 KiB holds the header, up to
-// kStaticMaxImages image descriptors, kStaticMaxItems work items and the
-// per-CTA offsets for up to kStaticMaxCtas CTAs.
+// Capacity of the static scratch: 512 KiB holds the header (the error word at
+// byte 0, the launch's two work counters at byte 16: runs claimed, CTAs
+// finished; zero when the library loads, reset by each launch's last CTA), up
+// to kStaticMaxImages image descriptors and kStaticMaxItems work items.
 constexpr int kStaticMaxImages = 128;
 constexpr int kStaticMaxItems = 16384;
 constexpr int kStaticMaxCtas = 2048;
-constexpr size_t kStaticHeader = 256;                         // error word
+constexpr size_t kStaticHeader = 256;
+constexpr size_t kStaticWorkOff = 16;
 constexpr size_t kStaticImgOff = kStaticHeader;
 constexpr size_t kStaticItemOff = kStaticImgOff + kStaticMaxImages * sizeof(BatchImage);
-constexpr size_t kStaticFirstOff = kStaticItemOff + kStaticMaxItems * sizeof(BatchItem);
 constexpr size_t kStaticBytes = 512 * 1024;
-static_assert(kStaticFirstOff + (kStaticMaxCtas + 1) * sizeof(int32_t) <= kStaticBytes, "static scratch too small");
+static_assert(kStaticItemOff + kStaticMaxItems * sizeof(BatchItem) <= kStaticBytes, "static scratch too small");
 
 static __device__ __align__(256) uint8_t g_static_scratch[kStaticBytes];
 
@@ -52,7 +54,12 @@ namespace {
 // a mutex while a call fills it; the upload copies it before the call returns.
 alignas(256) uint8_t t_host_stage[kStaticBytes];
 Geometry t_geo[kStaticMaxImages];
-int t_cls_items[kStaticMaxCtas];
+struct Cut {
+    BatchItem it;
+    double cost;
+    int order;
+};
+Cut t_cuts[kStaticMaxItems];
 std::mutex t_stage_mu;
 
 uint8_t *g_dev_addr[64];   // device address of g_static_scratch per device (null: not set up)
@@ -131,8 +138,11 @@ jdec_status decode_batch_static(const jdec_image *imgs, int n, cudaStream_t s)
     U.total = U.off_flag + 16 + 1024;
     const int occ = batch_occupancy(U.total);
 
-    // cost-balanced work list, one variant class after another (as the
-    // context-owned batch path), written straight into the staging image
+    // work list, one variant class after another: strip-row runs of at most a
+    // sixth of an even share of the class's cost per CTA, costliest first
+    // (as the context-owned batch path), claimed by the CTAs from the
+    // launch's counter; when that makes more runs than the static array
+    // holds, longer runs (a third of a share, then a whole share)
     long total_rows = 0;
     for (int i = 0; i < n; ++i) {
         const Geometry &g = t_geo[i];
@@ -141,22 +151,12 @@ jdec_status decode_batch_static(const jdec_image *imgs, int n, cudaStream_t s)
     const int nctas = static_cast<int>(std::max<long>(
         1, std::min<long>(std::min<long>(static_cast<long>(occ) * sms, total_rows), kStaticMaxCtas)));
     BatchItem *items = reinterpret_cast<BatchItem *>(h + kStaticItemOff);
-    int32_t *first = reinterpret_cast<int32_t *>(h + kStaticFirstOff);
-    // pass 1: count items per CTA; pass 2: place them (CTA-major order)
-    for (int pass = 0; pass < 2; ++pass) {
-        if (pass == 1) {
-            int acc = 0;
-            for (int c = 0; c < nctas; ++c) {
-                first[c] = acc;
-                acc += t_cls_items[c];
-                t_cls_items[c] = first[c];   // becomes the write cursor
-            }
-            first[nctas] = acc;
-            if (acc > kStaticMaxItems) return JDEC_EINVAL;   // work list exceeds the static scratch
-        } else {
-            for (int c = 0; c < nctas; ++c) t_cls_items[c] = 0;
-        }
-        for (int cls = 0; cls < kClasses; ++cls) {
+    int nitems = 0;
+    bool fits = false;
+    for (const double div : {6.0, 3.0, 1.0}) {
+        nitems = 0;
+        fits = true;
+        for (int cls = 0; cls < kClasses && fits; ++cls) {
             double total = 0.0;
             for (int i = 0; i < n; ++i) {
                 const Geometry &g = t_geo[i];
@@ -168,41 +168,43 @@ jdec_status decode_batch_static(const jdec_image *imgs, int n, cudaStream_t s)
                              g.mcus_y;
             }
             if (total <= 0.0) continue;
-            const double share = total / nctas;
-            int cta = 0;
-            double acc = 0.0;
-            for (int i = 0; i < n; ++i) {
+            const double cap = total / nctas / div;
+            const int min_rows = (cls / kQModes == 4 || cls / kQModes == 6) ? 6 : 1;
+            const int c0 = nitems;
+            for (int i = 0; i < n && fits; ++i) {
                 const Geometry &g = t_geo[i];
                 if (kQModes * hi[i].variant + hi[i].desc.qmode != cls) continue;
                 const int wt = hi[i].desc.wt;
                 const int ns = (g.mcus_x + wt - 1) / wt;
-                for (int stp = 0; stp < ns; ++stp) {
+                for (int stp = 0; stp < ns && fits; ++stp) {
                     const double rc = 64.0 * g.hm * g.vm * std::min(wt, g.mcus_x - stp * wt) *
                                       static_px_weight(hi[i].variant);
-                    int r = 0;
-                    while (r < g.mcus_y) {
-                        int take = g.mcus_y - r;
-                        if (cta < nctas - 1) {
-                            const int fit = static_cast<int>(((cta + 1) * share - acc) / rc + 0.5);
-                            take = std::max(1, std::min(take, fit));
+                    const int per = std::max(min_rows, static_cast<int>(cap / rc));
+                    for (int r = 0; r < g.mcus_y;) {
+                        if (nitems >= kStaticMaxItems) {
+                            fits = false;
+                            break;
                         }
-                        if (pass == 0) {
-                            ++t_cls_items[cta];
-                        } else {
-                            items[t_cls_items[cta]++] = BatchItem{i, stp, r, r + take};
-                        }
+                        const int take = std::min(g.mcus_y - r, per);
+                        t_cuts[nitems] = Cut{BatchItem{i, stp, r, r + take}, take * rc, nitems};
+                        ++nitems;
                         r += take;
-                        acc += take * rc;
-                        if (cta < nctas - 1 && acc >= (cta + 1) * share - 0.5 * rc) ++cta;
                     }
                 }
             }
+            if (fits)
+                std::sort(t_cuts + c0, t_cuts + nitems, [](const Cut &a, const Cut &b) {
+                    return a.cost != b.cost ? a.cost > b.cost : a.order < b.order;
+                });
         }
+        if (fits) break;
     }
+    if (!fits) return JDEC_EINVAL;   // work list exceeds the static scratch
+    for (int k = 0; k < nitems; ++k) items[k] = t_cuts[k].it;
 
     // upload (pageable host memory: the runtime stages it, nothing is
     // allocated here), clear the error word, launch
-    const size_t bytes = kStaticFirstOff + static_cast<size_t>(nctas + 1) * sizeof(int32_t);
+    const size_t bytes = kStaticItemOff + static_cast<size_t>(nitems) * sizeof(BatchItem);
     if (cudaMemsetAsync(dscratch, 0, sizeof(int), s) != cudaSuccess) return JDEC_ECUDA;
     if (cudaMemcpyAsync(dscratch + kStaticImgOff, h + kStaticImgOff, bytes - kStaticImgOff, cudaMemcpyHostToDevice,
                         s) != cudaSuccess)
@@ -210,12 +212,11 @@ jdec_status decode_batch_static(const jdec_image *imgs, int n, cudaStream_t s)
     BatchParams p;
     p.imgs = reinterpret_cast<const BatchImage *>(dscratch + kStaticImgOff);
     p.items = reinterpret_cast<const BatchItem *>(dscratch + kStaticItemOff);
-    p.cta_first = reinterpret_cast<const int32_t *>(dscratch + kStaticFirstOff);
     p.U = U;
     p.err = reinterpret_cast<int *>(dscratch);
-    p.work = nullptr;
+    p.work = reinterpret_cast<int *>(dscratch + kStaticWorkOff);
     p.item0 = 0;
-    p.nitems = 0;
+    p.nitems = nitems;
     if (launch_batch(p, nctas, U.total, s) != cudaSuccess) return JDEC_ECUDA;
     return JDEC_OK;
 }
