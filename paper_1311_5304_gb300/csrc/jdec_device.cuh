@@ -142,16 +142,31 @@ __device__ __forceinline__ uint32_t pack_sat4(int a, int b, int c, int d)
 
 // ---------------------------------------------------------------------------
 // 1-D transform (see the header comment).  `rnd` is added to the even
-// butterfly inputs, so every output carries it exactly once.
+// butterfly inputs, so every output carries it exactly once.  EVEN_ALU: the
+// even half leans on the integer ALU instead of the multiply pipe -- the 2^13
+// scaling as shifts, the x2/x6 rotation through one shared product
+// (4433 (x2 + x6) + 6270 x2 = 10703 x2 + 4433 x6 and 4433 (x2 + x6) - 15137 x6
+// = 4433 x2 - 10704 x6, identical mod 2^32); measured faster for the 4:4:4
+// kernel only, whose IDCT warps run beside a colour warp.
 // ---------------------------------------------------------------------------
+template <bool EVEN_ALU = false>
 __device__ __forceinline__ void idct8(const int x0, const int x1, const int x2, const int x3,
                                       const int x4, const int x5, const int x6, const int x7,
                                       const int rnd, int y[8])
 {
-    const int a0 = (x0 + x4) * 8192 + rnd;
-    const int a1 = (x0 - x4) * 8192 + rnd;
-    const int b0 = x2 * 10703 + x6 * 4433;
-    const int b1 = x2 * 4433 - x6 * 10704;
+    int a0, a1, b0, b1;
+    if constexpr (EVEN_ALU) {
+        a0 = ((x0 + x4) << 13) + rnd;
+        a1 = ((x0 - x4) << 13) + rnd;
+        const int z1 = (x2 + x6) * 4433;
+        b0 = z1 + x2 * 6270;
+        b1 = z1 - x6 * 15137;
+    } else {
+        a0 = (x0 + x4) * 8192 + rnd;
+        a1 = (x0 - x4) * 8192 + rnd;
+        b0 = x2 * 10703 + x6 * 4433;
+        b1 = x2 * 4433 - x6 * 10704;
+    }
     const int o0 = x1 * 11363 + x3 * 9633 + x5 * 6437 + x7 * 2260;
     const int o1 = x1 * 9633 - x3 * 2259 - x5 * 11362 - x7 * 6436;
     const int o2 = x1 * 6437 - x3 * 11362 + x5 * 2261 + x7 * 9633;
@@ -185,12 +200,13 @@ __device__ __forceinline__ int dp2a_hi(uint32_t a, uint32_t b, int c)
 
 // Row pass (Eq. 2) from the column-pass workspace, level shift and
 // range-limit clamp; 8 samples per row to dst.
+template <bool EVEN_ALU = false>
 __device__ __forceinline__ void idct_rows(const int ws[8][8], uint8_t *dst, int pitch)
 {
 #pragma unroll
     for (int yy = 0; yy < 8; ++yy) {
         int y[8];
-        idct8(ws[yy][0], ws[yy][1], ws[yy][2], ws[yy][3], ws[yy][4], ws[yy][5], ws[yy][6], ws[yy][7],
+        idct8<EVEN_ALU>(ws[yy][0], ws[yy][1], ws[yy][2], ws[yy][3], ws[yy][4], ws[yy][5], ws[yy][6], ws[yy][7],
               (1 << 17) + (128 << 18), y);
         uint2 out;
         out.x = pack_sat4(y[0] >> 18, y[1] >> 18, y[2] >> 18, y[3] >> 18);
@@ -206,6 +222,7 @@ __device__ __forceinline__ void idct_rows(const int ws[8][8], uint8_t *dst, int 
 // so each column's eight steps are two 16-byte loads.  Writes the 8x8
 // samples to `dst` (shared memory, row pitch `pitch` bytes, 8-byte aligned
 // rows).
+template <bool EVEN_ALU = false>
 __device__ __forceinline__ void idct_block(uint32_t blk, const int *__restrict__ qt, uint8_t *dst, int pitch)
 {
     const uint32_t sw = (blk >> 7) & 7u;
@@ -229,17 +246,18 @@ __device__ __forceinline__ void idct_block(uint32_t blk, const int *__restrict__
             x[v] = ((u & 1) ? sext_hi(word) : sext_lo(word)) * qv[v];
         }
         int y[8];
-        idct8(x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7], 1 << 10, y);
+        idct8<EVEN_ALU>(x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7], 1 << 10, y);
 #pragma unroll
         for (int yy = 0; yy < 8; ++yy) ws[yy][u] = y[yy] >> 11;
     }
     // Eq. 2: row pass over u for each spatial row, level shift, clamp.
-    idct_rows(ws, dst, pitch);
+    idct_rows<EVEN_ALU>(ws, dst, pitch);
 }
 
 // Same transform for quantisation steps that fit in 8 bits: sign extension
 // and dequantisation of a coefficient pair take one dp2a each.  qw: 32 words,
 // qw[8*p + v] = Q(2p, v) | Q(2p+1, v) << 24 (column pair p, row v).
+template <bool EVEN_ALU = false>
 __device__ __forceinline__ void idct_block_q8(uint32_t blk, const uint32_t *__restrict__ qw, uint8_t *dst, int pitch)
 {
     const uint32_t sw = (blk >> 7) & 7u;
@@ -262,14 +280,14 @@ __device__ __forceinline__ void idct_block_q8(uint32_t blk, const uint32_t *__re
             xh[v] = dp2a_hi(w[v][p], qv[v], 0);
         }
         int y[8];
-        idct8(xl[0], xl[1], xl[2], xl[3], xl[4], xl[5], xl[6], xl[7], 1 << 10, y);
+        idct8<EVEN_ALU>(xl[0], xl[1], xl[2], xl[3], xl[4], xl[5], xl[6], xl[7], 1 << 10, y);
 #pragma unroll
         for (int yy = 0; yy < 8; ++yy) ws[yy][2 * p] = y[yy] >> 11;
-        idct8(xh[0], xh[1], xh[2], xh[3], xh[4], xh[5], xh[6], xh[7], 1 << 10, y);
+        idct8<EVEN_ALU>(xh[0], xh[1], xh[2], xh[3], xh[4], xh[5], xh[6], xh[7], 1 << 10, y);
 #pragma unroll
         for (int yy = 0; yy < 8; ++yy) ws[yy][2 * p + 1] = y[yy] >> 11;
     }
-    idct_rows(ws, dst, pitch);
+    idct_rows<EVEN_ALU>(ws, dst, pitch);
 }
 
 // ---------------------------------------------------------------------------

@@ -324,16 +324,17 @@ __device__ __forceinline__ void load_qtables(int *qs, const ImageDesc &d, int ti
     }
 }
 
-// One dequantisation + IDCT task (block at shared address blk -> samples at dst).
-template <int QM>
+// One dequantisation + IDCT task (block at shared address blk -> samples at
+// dst); EVEN_ALU as for idct8 (the LLM forms).
+template <int QM, bool EVEN_ALU = false>
 __device__ __forceinline__ void idct_task(uint32_t blk, const int *q, uint8_t *dst, int pitch)
 {
     if (QM == kQ8)
-        idct_block_q8(blk, reinterpret_cast<const uint32_t *>(q), dst, pitch);
+        idct_block_q8<EVEN_ALU>(blk, reinterpret_cast<const uint32_t *>(q), dst, pitch);
     else if (QM == kAAN)
         idct_block_aan(blk, q, dst, pitch);
     else
-        idct_block(blk, q, dst, pitch);
+        idct_block<EVEN_ALU>(blk, q, dst, pitch);
 }
 
 // The IDCT tasks of one job on threads [0, nthr) (this thread: tid), any
@@ -366,7 +367,7 @@ __device__ __forceinline__ void idct_job(uint8_t *stage, uint8_t *yplane, uint8_
             dst = slot + comp * 8 * L.lc + 8 * lb;
             pitch = L.lc;
         }
-        idct_task<QM>(blk, q, dst, pitch);
+        idct_task<QM, HM == 1 && VM == 1>(blk, q, dst, pitch);
     }
 }
 
@@ -420,7 +421,8 @@ struct FixedIdct {
             if (t >= NTASK) break;
             const bool luma = t < NY;
             if (luma ? !has_y : !has_c) continue;
-            idct_task<QM>(smem_u32(stage + src[i]), qs + qoff[i], (luma ? yplane : slot) + dst[i], pitch[i]);
+            idct_task<QM, HM == 1 && VM == 1>(smem_u32(stage + src[i]), qs + qoff[i], (luma ? yplane : slot) + dst[i],
+                                              pitch[i]);
         }
     }
 };
